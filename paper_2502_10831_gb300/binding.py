@@ -1,0 +1,266 @@
+"""ctypes binding of libptrig's C ABI (include/ptrig.h), same names as the C
+entry points.  Argument marshalling only: every computation runs in the CUDA
+library.  Arguments may be torch tensors (their data pointer and element count
+are used) or raw integer addresses; `stream` defaults to torch's current CUDA
+stream.  A nonzero status raises PtrigError.
+
+The library must have been built (python -m paper_2502_10831_gb300.build);
+loading fails loudly otherwise -- there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libptrig.so")
+
+SIN, COS, TAN, SINCOS = 0, 1, 2, 3
+FAMILY_F32, FAMILY_HALF, FAMILY_TAYLOR, FAMILY_BWD = 0, 1, 2, 3
+BATCH_GRAPH = 1
+
+_P = ctypes.c_void_p
+_SZ = ctypes.c_size_t
+_I = ctypes.c_int
+
+# name -> argument types (all return ptrig_status as int unless listed in _RESTYPE)
+SIGNATURES = {
+    "ptrig_status_string": [_I],
+    "ptrig_last_cuda_error": [],
+    "ptrig_version": [],
+    "ptrig_sin_f32": [_P, _P, _SZ, _P],
+    "ptrig_cos_f32": [_P, _P, _SZ, _P],
+    "ptrig_tan_f32": [_P, _P, _SZ, _P],
+    "ptrig_sincos_f32": [_P, _P, _P, _SZ, _P],
+    "ptrig_sin_f16": [_P, _P, _SZ, _P],
+    "ptrig_cos_f16": [_P, _P, _SZ, _P],
+    "ptrig_tan_f16": [_P, _P, _SZ, _P],
+    "ptrig_sincos_f16": [_P, _P, _P, _SZ, _P],
+    "ptrig_sin_bf16": [_P, _P, _SZ, _P],
+    "ptrig_cos_bf16": [_P, _P, _SZ, _P],
+    "ptrig_tan_bf16": [_P, _P, _SZ, _P],
+    "ptrig_sincos_bf16": [_P, _P, _P, _SZ, _P],
+    "ptrig_sin_f64": [_P, _P, _SZ, _P],
+    "ptrig_cos_f64": [_P, _P, _SZ, _P],
+    "ptrig_tan_f64": [_P, _P, _SZ, _P],
+    "ptrig_taylor_sin_f32": [_P, _P, _SZ, _P],
+    "ptrig_taylor_cos_f32": [_P, _P, _SZ, _P],
+    "ptrig_taylor_tan_f32": [_P, _P, _SZ, _P],
+    "ptrig_taylor_n_f32": [_I, _I, _P, _P, _SZ, _P],
+    "ptrig_sin_bwd_f32": [_P, _P, _P, _SZ, _P],
+    "ptrig_cos_bwd_f32": [_P, _P, _P, _SZ, _P],
+    "ptrig_tan_bwd_f32": [_P, _P, _P, _SZ, _P],
+    "ptrig_sin_bwd_f64": [_P, _P, _P, _SZ, _P],
+    "ptrig_cos_bwd_f64": [_P, _P, _P, _SZ, _P],
+    "ptrig_tan_bwd_f64": [_P, _P, _P, _SZ, _P],
+    "ptrig_segment_f32": [_P, _P, _SZ, _P],
+    "ptrig_cudamath_f32": [_I, _I, _P, _P, _P, _SZ, _P],
+    "ptrig_set_launch_config": [_I, _I, _I, _I],
+    "ptrig_get_launch_config": [_I, _P, _P, _P],
+    "ptrig_batch_plan_create": [_P, _P, _SZ, _I],
+    "ptrig_batch_run": [_P, _P],
+    "ptrig_batch_run_per_array": [_P, _P],
+    "ptrig_batch_plan_set_config": [_P, _I, _I],
+    "ptrig_batch_plan_get_config": [_P, _P, _P, _P, _P],
+    "ptrig_batch_plan_autotune": [_P, _P, _I, _P, _P, _I, _P, _P, _P],
+    "ptrig_batch_plan_destroy": [_P],
+}
+_RESTYPE = {"ptrig_status_string": ctypes.c_char_p, "ptrig_batch_plan_destroy": None}
+
+
+class PtrigError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        lib = _load()
+        msg = lib.ptrig_status_string(status).decode()
+        if status == 2:
+            msg += f" (cudaError {lib.ptrig_last_cuda_error()})"
+        super().__init__(f"{where}: {msg}")
+
+
+class ptrig_desc(ctypes.Structure):
+    """Mirror of the C struct ptrig_desc (40 bytes)."""
+    _fields_ = [("x", ctypes.c_void_p), ("y0", ctypes.c_void_p), ("y1", ctypes.c_void_p),
+                ("n", ctypes.c_uint64), ("func", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        with _lock:
+            if _lib is None:
+                if not os.path.exists(LIB_PATH):
+                    raise ImportError(
+                        f"libptrig.so is not built ({LIB_PATH}); run "
+                        "`python -m paper_2502_10831_gb300.build` (needs nvcc). "
+                        "There is no CPU fallback.")
+                L = ctypes.CDLL(LIB_PATH)
+                for name, args in SIGNATURES.items():
+                    f = getattr(L, name)
+                    f.argtypes = args
+                    f.restype = _RESTYPE.get(name, ctypes.c_int)
+                _lib = L
+    return _lib
+
+
+def lib():
+    """The loaded ctypes library (raises ImportError if it was not built)."""
+    return _load()
+
+
+def exported_symbols() -> list[str]:
+    return list(SIGNATURES)
+
+
+# --------------------------------------------------------------- marshalling
+
+
+def _ptr(a) -> int | None:
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    return a.data_ptr()
+
+
+def _count(a) -> int:
+    return a.numel()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise PtrigError(status, where)
+
+
+def _unary(name):
+    def f(x, y, n=None, stream=None):
+        n = _count(x) if n is None else n
+        _check(getattr(_load(), name)(_ptr(x), _ptr(y), n, _stream(stream)), name)
+    f.__name__ = name
+    f.__doc__ = f"{name}(x, y, n=None, stream=None): see include/ptrig.h"
+    return f
+
+
+def _binary_out(name):
+    def f(x, y0, y1, n=None, stream=None):
+        n = _count(x) if n is None else n
+        _check(getattr(_load(), name)(_ptr(x), _ptr(y0), _ptr(y1), n, _stream(stream)), name)
+    f.__name__ = name
+    f.__doc__ = f"{name}(x, a, b, n=None, stream=None): see include/ptrig.h"
+    return f
+
+
+for _name, _args in SIGNATURES.items():
+    if _args == [_P, _P, _SZ, _P]:
+        globals()[_name] = _unary(_name)
+    elif _args == [_P, _P, _P, _SZ, _P]:
+        globals()[_name] = _binary_out(_name)
+
+
+def ptrig_taylor_n_f32(func, nterms, x, y, n=None, stream=None):
+    n = _count(x) if n is None else n
+    _check(_load().ptrig_taylor_n_f32(func, nterms, _ptr(x), _ptr(y), n, _stream(stream)),
+           "ptrig_taylor_n_f32")
+
+
+def ptrig_cudamath_f32(func, fast, x, y0, y1=None, n=None, stream=None):
+    n = _count(x) if n is None else n
+    _check(_load().ptrig_cudamath_f32(func, fast, _ptr(x), _ptr(y0), _ptr(y1), n, _stream(stream)),
+           "ptrig_cudamath_f32")
+
+
+def ptrig_status_string(status: int) -> str:
+    return _load().ptrig_status_string(status).decode()
+
+
+def ptrig_last_cuda_error() -> int:
+    return _load().ptrig_last_cuda_error()
+
+
+def ptrig_version() -> int:
+    return _load().ptrig_version()
+
+
+def ptrig_set_launch_config(family, block, vec_per_thread, blocks_per_sm):
+    _check(_load().ptrig_set_launch_config(family, block, vec_per_thread, blocks_per_sm),
+           "ptrig_set_launch_config")
+
+
+def ptrig_get_launch_config(family):
+    b, v, s = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(_load().ptrig_get_launch_config(family, ctypes.byref(b), ctypes.byref(v), ctypes.byref(s)),
+           "ptrig_get_launch_config")
+    return b.value, v.value, s.value
+
+
+# ----------------------------------------------------------------- batch
+
+
+class BatchPlan:
+    """Owner of a ptrig_batch_plan: descriptors of (x, y0, y1, n, func)."""
+
+    def __init__(self, descs, flags: int = 0):
+        arr = (ptrig_desc * len(descs))()
+        for i, (x, y0, y1, n, func) in enumerate(descs):
+            arr[i] = ptrig_desc(_ptr(x), _ptr(y0), _ptr(y1), int(n), int(func), 0)
+        self._keep = arr
+        self.handle = ctypes.c_void_p()
+        _check(_load().ptrig_batch_plan_create(ctypes.byref(self.handle), arr, len(descs), flags),
+               "ptrig_batch_plan_create")
+
+    def run(self, stream=None):
+        _check(_load().ptrig_batch_run(self.handle, _stream(stream)), "ptrig_batch_run")
+
+    def run_per_array(self, stream=None):
+        _check(_load().ptrig_batch_run_per_array(self.handle, _stream(stream)), "ptrig_batch_run_per_array")
+
+    def set_config(self, block: int, items_per_thread: int):
+        _check(_load().ptrig_batch_plan_set_config(self.handle, block, items_per_thread),
+               "ptrig_batch_plan_set_config")
+
+    def config(self):
+        b, it, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        t = ctypes.c_uint64()
+        _check(_load().ptrig_batch_plan_get_config(self.handle, ctypes.byref(b), ctypes.byref(it),
+                                                   ctypes.byref(t), ctypes.byref(g)),
+               "ptrig_batch_plan_get_config")
+        return {"block": b.value, "items_per_thread": it.value, "tiles": t.value, "grid": g.value}
+
+    def autotune(self, reps: int = 5, candidates=None, stream=None):
+        bb, bi, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        if candidates:
+            cb = (ctypes.c_int * len(candidates))(*[c[0] for c in candidates])
+            ci = (ctypes.c_int * len(candidates))(*[c[1] for c in candidates])
+            nc = len(candidates)
+        else:
+            cb = ci = None
+            nc = 0
+        _check(_load().ptrig_batch_plan_autotune(self.handle, _stream(stream), reps, cb, ci, nc,
+                                                 ctypes.byref(bb), ctypes.byref(bi), ctypes.byref(ms)),
+               "ptrig_batch_plan_autotune")
+        return {"block": bb.value, "items_per_thread": bi.value, "ms": ms.value}
+
+    def close(self):
+        if self.handle:
+            _load().ptrig_batch_plan_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,331 @@
+// ptrig_batch.cu -- ragged batch: thousands of arrays, each with its own
+// function selector, evaluated by ONE persistent kernel launch.
+//
+// The plan cuts every array into tiles of block * items_per_thread elements
+// and keeps a tile -> array map in device memory, so a block finds its array
+// with a single load.  Blocks walk the tile list round-robin (tile = blockIdx,
+// blockIdx + grid, ...); a tile's selector is uniform over the block, so the
+// switch on it never diverges.  The grid is the SM count times the kernel's
+// occupancy.  With PTRIG_BATCH_GRAPH the launch is captured once into a CUDA
+// graph and ptrig_batch_run replays it.
+#include <algorithm>
+#include <vector>
+
+#include "ptrig_map.cuh"
+
+struct ptrig_batch_plan {
+  int device = -1;
+  unsigned flags = 0;
+  std::vector<ptrig_desc> host;
+  ptrig_desc *d_desc = nullptr;
+  uint32_t *d_owner = nullptr;
+  size_t owner_cap = 0;
+  uint64_t *d_first = nullptr;
+  uint64_t ntiles = 0;
+  int block = 256;
+  int items = 32;
+  int grid = 0;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace ptrig {
+
+static_assert(sizeof(ptrig_desc) == 40, "ptrig_desc layout");
+
+template <int OP>
+__device__ __forceinline__ void batch_tile(const ptrig_desc &d, uint64_t start, uint32_t len, const float4 *tab) {
+  using F = Proposed<OP>;
+  const float *x = d.x + start;
+  float *y0 = d.y0 + start;
+  float *y1 = (OP == OP_SINCOS) ? d.y1 + start : nullptr;
+  uintptr_t a = (uintptr_t)x | (uintptr_t)y0;
+  if (OP == OP_SINCOS) a |= (uintptr_t)y1;
+  uint32_t done = 0;
+  if ((a & 15u) == 0) {
+    constexpr int U = 2;  // vectors in flight per thread
+    const uint32_t nv = len / 4;
+    for (uint32_t v0 = threadIdx.x; v0 < nv; v0 += blockDim.x * U) {
+      uint4 in[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint32_t i = v0 + u * blockDim.x;
+        if (i < nv) in[u] = ld_stream(reinterpret_cast<const uint4 *>(x) + i);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint32_t i = v0 + u * blockDim.x;
+        if (i < nv) {
+          float f[4], o0[4], o1[4];
+          Storage<float>::unpack(in[u], f);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) F::eval(f[e], tab, o0[e], o1[e]);
+          st_stream(reinterpret_cast<uint4 *>(y0) + i, Storage<float>::pack(o0));
+          if constexpr (F::NOUT == 2) st_stream(reinterpret_cast<uint4 *>(y1) + i, Storage<float>::pack(o1));
+        }
+      }
+    }
+    done = nv * 4;
+  }
+  for (uint32_t i = done + threadIdx.x; i < len; i += blockDim.x) {
+    float o0, o1;
+    F::eval(__ldg(x + i), tab, o0, o1);
+    y0[i] = o0;
+    if constexpr (F::NOUT == 2) y1[i] = o1;
+  }
+}
+
+__global__ void __launch_bounds__(512) k_batch(const ptrig_desc *__restrict__ descs,
+                                               const uint32_t *__restrict__ owner,
+                                               const uint64_t *__restrict__ first_tile, uint64_t ntiles,
+                                               uint32_t tile_elems) {
+  __shared__ float4 s_tab[8];
+  if (threadIdx.x < 8) s_tab[threadIdx.x] = c_tab_f32[threadIdx.x];
+  __syncthreads();
+  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const uint32_t a = __ldg(owner + tile);
+    const ptrig_desc d = descs[a];
+    const uint64_t start = (tile - __ldg(first_tile + a)) * (uint64_t)tile_elems;
+    const uint64_t rem = d.n - start;
+    const uint32_t len = rem < tile_elems ? (uint32_t)rem : tile_elems;
+    switch (d.func) {
+      case PTRIG_SIN:
+        batch_tile<OP_SIN>(d, start, len, s_tab);
+        break;
+      case PTRIG_COS:
+        batch_tile<OP_COS>(d, start, len, s_tab);
+        break;
+      case PTRIG_TAN:
+        batch_tile<OP_TAN>(d, start, len, s_tab);
+        break;
+      default:
+        batch_tile<OP_SINCOS>(d, start, len, s_tab);
+        break;
+    }
+  }
+}
+
+static void free_graph(ptrig_batch_plan *p) {
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  p->exec = nullptr;
+  p->graph = nullptr;
+}
+
+static ptrig_status launch_batch(ptrig_batch_plan *p, cudaStream_t s) {
+  if (p->ntiles == 0) return PTRIG_OK;
+  k_batch<<<p->grid, p->block, 0, s>>>(p->d_desc, p->d_owner, p->d_first, p->ntiles,
+                                        (uint32_t)(p->block * p->items));
+  return finish_launch();
+}
+
+static ptrig_status capture_graph(ptrig_batch_plan *p) {
+  free_graph(p);
+  if (!(p->flags & PTRIG_BATCH_GRAPH) || p->ntiles == 0) return PTRIG_OK;
+  cudaError_t e;
+  if (!p->cap_stream) {
+    e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(e);
+  const ptrig_status st = launch_batch(p, p->cap_stream);
+  e = cudaStreamEndCapture(p->cap_stream, &p->graph);
+  if (st != PTRIG_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return PTRIG_OK;
+}
+
+// Rebuilds the tile map for the plan's (block, items) and uploads it.
+static ptrig_status build_tiles(ptrig_batch_plan *p) {
+  const uint64_t tile = (uint64_t)p->block * (uint64_t)p->items;
+  std::vector<uint64_t> first(p->host.size() + 1);
+  uint64_t nt = 0;
+  for (size_t i = 0; i < p->host.size(); ++i) {
+    first[i] = nt;
+    nt += (p->host[i].n + tile - 1) / tile;
+  }
+  first[p->host.size()] = nt;
+  if (nt > 0xffffffffull) return PTRIG_ERR_INVALID_ARG;
+  std::vector<uint32_t> owner((size_t)nt);
+  for (size_t i = 0; i < p->host.size(); ++i)
+    for (uint64_t t = first[i]; t < first[i + 1]; ++t) owner[(size_t)t] = (uint32_t)i;
+  cudaError_t e;
+  if (nt > p->owner_cap) {
+    if (p->d_owner) cudaFree(p->d_owner);
+    p->d_owner = nullptr;
+    p->owner_cap = 0;
+    e = cudaMalloc(&p->d_owner, std::max<size_t>((size_t)nt, 1) * sizeof(uint32_t));
+    if (e != cudaSuccess) return cuda_fail(e);
+    p->owner_cap = (size_t)nt;
+  }
+  if (nt > 0) {
+    e = cudaMemcpy(p->d_owner, owner.data(), (size_t)nt * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e);
+  }
+  e = cudaMemcpy(p->d_first, first.data(), first.size() * sizeof(uint64_t), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e);
+  p->ntiles = nt;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch, p->block, 0);
+  if (e != cudaSuccess) return cuda_fail(e);
+  const int sms = sm_count();
+  if (sms <= 0) return PTRIG_ERR_NO_DEVICE;
+  const uint64_t g = std::min<uint64_t>((uint64_t)sms * (uint64_t)std::max(occ, 1), std::max<uint64_t>(nt, 1));
+  p->grid = (int)g;
+  return capture_graph(p);
+}
+
+}  // namespace ptrig
+
+using namespace ptrig;
+
+extern "C" {
+
+ptrig_status ptrig_batch_plan_create(ptrig_batch_plan **plan, const ptrig_desc *host_descs, size_t count,
+                                     int flags) {
+  if (!plan) return PTRIG_ERR_INVALID_ARG;
+  *plan = nullptr;
+  if (count > 0 && !host_descs) return PTRIG_ERR_INVALID_ARG;
+  if (count > 0xffffffffull) return PTRIG_ERR_INVALID_ARG;
+  if (flags & ~(int)PTRIG_BATCH_GRAPH) return PTRIG_ERR_INVALID_ARG;
+  for (size_t i = 0; i < count; ++i) {
+    const ptrig_desc &d = host_descs[i];
+    if (d.func > PTRIG_SINCOS || d.reserved != 0) return PTRIG_ERR_INVALID_ARG;
+    if (d.n > 0 && (!d.x || !d.y0 || (d.func == PTRIG_SINCOS && !d.y1))) return PTRIG_ERR_INVALID_ARG;
+    if (d.n > (1ull << 62)) return PTRIG_ERR_INVALID_ARG;
+  }
+  if (sm_count() <= 0) return PTRIG_ERR_NO_DEVICE;
+  ptrig_batch_plan *p = new ptrig_batch_plan();
+  p->flags = (unsigned)flags;
+  cudaGetDevice(&p->device);
+  p->host.assign(host_descs, host_descs + count);
+  cudaError_t e = cudaMalloc(&p->d_desc, std::max<size_t>(count, 1) * sizeof(ptrig_desc));
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_first, (count + 1) * sizeof(uint64_t));
+  if (e == cudaSuccess && count > 0)
+    e = cudaMemcpy(p->d_desc, p->host.data(), count * sizeof(ptrig_desc), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    ptrig_batch_plan_destroy(p);
+    return cuda_fail(e);
+  }
+  const ptrig_status st = build_tiles(p);
+  if (st != PTRIG_OK) {
+    ptrig_batch_plan_destroy(p);
+    return st;
+  }
+  *plan = p;
+  return PTRIG_OK;
+}
+
+ptrig_status ptrig_batch_run(ptrig_batch_plan *plan, ptrig_stream stream) {
+  if (!plan) return PTRIG_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (plan->exec) {
+    const cudaError_t e = cudaGraphLaunch(plan->exec, s);
+    return e == cudaSuccess ? PTRIG_OK : cuda_fail(e);
+  }
+  return launch_batch(plan, s);
+}
+
+ptrig_status ptrig_batch_run_per_array(ptrig_batch_plan *plan, ptrig_stream stream) {
+  if (!plan) return PTRIG_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  for (const ptrig_desc &d : plan->host) {
+    if (d.n == 0) continue;
+    const ptrig_status st = launch_proposed_f32((int)d.func, d.x, d.y0, d.y1, (size_t)d.n, s);
+    if (st != PTRIG_OK) return st;
+  }
+  return PTRIG_OK;
+}
+
+ptrig_status ptrig_batch_plan_set_config(ptrig_batch_plan *plan, int block, int items_per_thread) {
+  if (!plan) return PTRIG_ERR_INVALID_ARG;
+  const int b = block ? block : plan->block;
+  const int it = items_per_thread ? items_per_thread : plan->items;
+  if (b < 64 || b > 512 || b % 32 != 0 || it < 4 || it > 256 || it % 4 != 0) return PTRIG_ERR_INVALID_ARG;
+  plan->block = b;
+  plan->items = it;
+  return build_tiles(plan);
+}
+
+ptrig_status ptrig_batch_plan_get_config(const ptrig_batch_plan *plan, int *block, int *items_per_thread,
+                                         uint64_t *tiles, int *grid) {
+  if (!plan) return PTRIG_ERR_INVALID_ARG;
+  if (block) *block = plan->block;
+  if (items_per_thread) *items_per_thread = plan->items;
+  if (tiles) *tiles = plan->ntiles;
+  if (grid) *grid = plan->grid;
+  return PTRIG_OK;
+}
+
+ptrig_status ptrig_batch_plan_autotune(ptrig_batch_plan *plan, ptrig_stream stream, int reps,
+                                       const int *cand_block, const int *cand_items, int ncand,
+                                       int *best_block, int *best_items, float *best_ms) {
+  if (!plan || reps < 1 || ncand < 0 || (ncand > 0 && (!cand_block || !cand_items))) return PTRIG_ERR_INVALID_ARG;
+  static const int kBlocks[] = {128, 256, 256, 512, 512, 256, 128, 512};
+  static const int kItems[] = {32, 16, 32, 8, 16, 64, 64, 32};
+  const int nc = ncand ? ncand : (int)(sizeof(kBlocks) / sizeof(kBlocks[0]));
+  const int *cb = ncand ? cand_block : kBlocks;
+  const int *ci = ncand ? cand_items : kItems;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(e);
+  }
+  const unsigned saved_flags = plan->flags;
+  plan->flags &= ~PTRIG_BATCH_GRAPH;  // time plain launches while searching
+  float best = -1.0f;
+  int bb = plan->block, bi = plan->items;
+  ptrig_status st = PTRIG_OK;
+  for (int c = 0; c < nc && st == PTRIG_OK; ++c) {
+    st = ptrig_batch_plan_set_config(plan, cb[c], ci[c]);
+    if (st != PTRIG_OK) break;
+    st = launch_batch(plan, s);
+    if (st != PTRIG_OK) break;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < reps && st == PTRIG_OK; ++r) st = launch_batch(plan, s);
+    cudaEventRecord(e1, s);
+    e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      st = cuda_fail(e);
+      break;
+    }
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= (float)reps;
+    if (best < 0.0f || ms < best) {
+      best = ms;
+      bb = plan->block;
+      bi = plan->items;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  plan->flags = saved_flags;
+  if (st != PTRIG_OK) return st;
+  st = ptrig_batch_plan_set_config(plan, bb, bi);
+  if (st != PTRIG_OK) return st;
+  if (best_block) *best_block = bb;
+  if (best_items) *best_items = bi;
+  if (best_ms) *best_ms = best;
+  return PTRIG_OK;
+}
+
+void ptrig_batch_plan_destroy(ptrig_batch_plan *plan) {
+  if (!plan) return;
+  free_graph(plan);
+  if (plan->cap_stream) cudaStreamDestroy(plan->cap_stream);
+  if (plan->d_desc) cudaFree(plan->d_desc);
+  if (plan->d_owner) cudaFree(plan->d_owner);
+  if (plan->d_first) cudaFree(plan->d_first);
+  delete plan;
+}
+
+}  // extern "C"

@@ -1,0 +1,37 @@
+// ptrig_internal.h -- host-side declarations shared by the libptrig translation
+// units (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "ptrig.h"
+
+namespace ptrig {
+
+struct LaunchCfg {
+  int block;          // threads per block
+  int vpt;            // 16-byte vectors per thread per iteration (1, 2, 4)
+  int blocks_per_sm;  // grid cap in blocks per SM, 0 = uncapped
+};
+
+LaunchCfg get_cfg(int family);
+int sm_count();                       // SMs of the current device, <= 0 if none
+ptrig_status finish_launch();         // checks the launch, records CUDA errors
+ptrig_status cuda_fail(cudaError_t e);  // records e, returns PTRIG_ERR_CUDA
+
+// Elementwise launchers (arguments already validated for NULL / n == 0).
+ptrig_status launch_proposed_f32(int op, const float *x, float *y0, float *y1, size_t n, cudaStream_t s);
+ptrig_status launch_proposed_f16(int op, const void *x, void *y0, void *y1, size_t n, cudaStream_t s);
+ptrig_status launch_proposed_bf16(int op, const void *x, void *y0, void *y1, size_t n, cudaStream_t s);
+ptrig_status launch_taylor_f32(int op, int nterms, const float *x, float *y, size_t n, cudaStream_t s);
+ptrig_status launch_bwd_f32(int op, const float *x, const float *gy, float *gx, size_t n, cudaStream_t s);
+ptrig_status launch_f64(int op, int bwd, const double *x, const double *gy, double *out, size_t n,
+                        cudaStream_t s);
+ptrig_status launch_segment_f32(const float *x, uint8_t *out, size_t n, cudaStream_t s);
+ptrig_status launch_cudamath_f32(int op, int fast, const float *x, float *y0, float *y1, size_t n,
+                                 cudaStream_t s);
+
+}  // namespace ptrig

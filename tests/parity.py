@@ -1,0 +1,69 @@
+"""Comparison rules between the CUDA library and the FP64 oracle.
+
+  * segment index: bit-exact, except within 2 FP32 ulps of a node k pi/12,
+    where the GPU may take the adjacent segment; its value is then compared
+    with the oracle's value of that adjacent segment's formula.
+  * quadrant: bit-exact.
+  * FP32 sin / cos: |delta| <= 1e-6.
+  * FP32 tan: relative error <= 1e-5 where |cos interpolant| >= 1e-3.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+SIN_COS_ATOL = 1e-6
+TAN_RTOL = 1e-5
+TAN_COS_FLOOR = 1e-3
+STEP = math.pi / 12
+
+
+def near_node(u: np.ndarray) -> np.ndarray:
+    """|u - m pi/12| within 2 FP32 ulps of the node (m = 1..5)."""
+    m = np.round(u / STEP)
+    node = m * STEP
+    ulp = np.spacing(np.abs(node).astype(np.float32)).astype(np.float64)
+    return (np.abs(u - node) <= 2 * ulp) & (m >= 1) & (m <= 5)
+
+
+def reference_with_gpu_segments(oracle, func: str, xd: np.ndarray, seg_gpu: np.ndarray):
+    """Oracle values evaluated with the segment the GPU chose (checked to be
+    the oracle's own segment or, near a node, an adjacent one)."""
+    u, q, neg, seg_o, _ = oracle.reduce(xd)
+    finite = np.isfinite(xd)
+    gseg = (seg_gpu & 0x0F).astype(np.int32)
+    gq = (seg_gpu >> 4).astype(np.int32)
+    assert np.all(seg_gpu[~finite] == 0xFF)
+    assert np.array_equal(gq[finite], q[finite]), "quadrant mismatch"
+    diff = finite & (gseg != seg_o)
+    nn = near_node(u)
+    bad = diff & ~(nn & (np.abs(gseg - seg_o) == 1))
+    assert not bad.any(), f"segment mismatch away from nodes at x={xd[bad][:5]}"
+    ref = oracle.proposed(func, xd)
+    for dk in (-1, 1):
+        m = diff & (gseg - seg_o == dk)
+        if m.any():
+            ref[m] = oracle.proposed_neighbour(func, dk, xd[m])
+    return ref, diff
+
+
+def check_values(oracle, func: str, xd: np.ndarray, y: np.ndarray, ref: np.ndarray,
+                 atol: float = SIN_COS_ATOL, rtol: float = TAN_RTOL):
+    finite = np.isfinite(xd)
+    assert np.all(np.isnan(y[~finite])), "NaN/inf input must give NaN"
+    yf = y[finite].astype(np.float64)
+    rf = ref[finite]
+    if func in ("sin", "cos"):
+        err = np.abs(yf - rf)
+        worst = int(np.argmax(err)) if err.size else 0
+        assert err.size == 0 or err.max() <= atol, (
+            f"{func}: max |delta| {err.max():.3e} at x={xd[finite][worst]!r}")
+        return float(err.max()) if err.size else 0.0
+    c = np.abs(oracle.proposed("cos", xd[finite]))
+    keep = c >= TAN_COS_FLOOR
+    rel = np.abs(yf[keep] - rf[keep]) / np.abs(rf[keep])
+    worst = int(np.argmax(rel)) if rel.size else 0
+    assert rel.size == 0 or rel.max() <= rtol, (
+        f"tan: max rel {rel.max():.3e} at x={xd[finite][keep][worst]!r}")
+    return float(rel.max()) if rel.size else 0.0

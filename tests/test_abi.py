@@ -1,0 +1,110 @@
+"""The C-ABI library builds, loads and exports every symbol include/ptrig.h
+declares; host-side argument checks answer without touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ptrig.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ptrig_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2502_10831_gb300 import build
+    build.build()
+    from paper_2502_10831_gb300 import binding
+    return binding.lib()
+
+
+def test_header_declares_the_scope_entry_points():
+    names = set(_declared())
+    for fn in ("sin", "cos", "tan"):
+        for dt in ("f32", "f16", "bf16", "f64"):
+            assert f"ptrig_{fn}_{dt}" in names
+        for dt in ("f32", "f64"):
+            assert f"ptrig_{fn}_bwd_{dt}" in names
+        assert f"ptrig_taylor_{fn}_f32" in names
+    for dt in ("f32", "f16", "bf16"):
+        assert f"ptrig_sincos_{dt}" in names
+    for n in ("ptrig_batch_plan_create", "ptrig_batch_run", "ptrig_batch_plan_destroy", "ptrig_status_string"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2502_10831_gb300 import binding
+    assert sorted(binding.exported_symbols()) == _declared()
+
+
+def test_status_strings(lib):
+    from paper_2502_10831_gb300 import binding
+    for s in range(5):
+        assert binding.ptrig_status_string(s).startswith("PTRIG")
+    assert "unknown" in binding.ptrig_status_string(99)
+
+
+def test_host_validation_without_gpu(lib):
+    """NULL pointers with n > 0 and bad selectors are rejected before any CUDA
+    call; n == 0 is a no-op."""
+    assert lib.ptrig_sin_f32(None, None, 0, None) == 0
+    for name in ("ptrig_sin_f32", "ptrig_cos_f16", "ptrig_tan_bf16", "ptrig_sin_f64", "ptrig_taylor_tan_f32"):
+        assert getattr(lib, name)(None, None, 4, None) == 1
+    assert lib.ptrig_sincos_f32(1024, 2048, None, 4, None) == 1
+    assert lib.ptrig_sin_bwd_f32(1024, None, 2048, 4, None) == 1
+    assert lib.ptrig_taylor_n_f32(0, 6, 1024, 2048, 4, None) == 1
+    assert lib.ptrig_taylor_n_f32(3, 5, 1024, 2048, 4, None) == 1
+    assert lib.ptrig_cudamath_f32(4, 0, 1024, 2048, None, 4, None) == 1
+    assert lib.ptrig_set_launch_config(0, 100, 4, 0) == 1
+    assert lib.ptrig_set_launch_config(0, 256, 3, 0) == 1
+    assert lib.ptrig_set_launch_config(7, 256, 4, 0) == 1
+
+
+def test_launch_config_roundtrip(lib):
+    from paper_2502_10831_gb300 import binding as B
+    old = B.ptrig_get_launch_config(B.FAMILY_TAYLOR)
+    B.ptrig_set_launch_config(B.FAMILY_TAYLOR, 128, 2, 4)
+    assert B.ptrig_get_launch_config(B.FAMILY_TAYLOR) == (128, 2, 4)
+    B.ptrig_set_launch_config(B.FAMILY_TAYLOR, *old)
+
+
+def test_batch_plan_rejects_bad_descriptors(lib):
+    from paper_2502_10831_gb300 import binding as B
+    h = ctypes.c_void_p()
+    bad = [
+        B.ptrig_desc(1024, 2048, 0, 10, 7, 0),      # unknown func
+        B.ptrig_desc(1024, 2048, 0, 10, 0, 1),      # reserved != 0
+        B.ptrig_desc(0, 2048, 0, 10, 0, 0),         # NULL x
+        B.ptrig_desc(1024, 2048, 0, 10, 3, 0),      # sincos without y1
+    ]
+    for d in bad:
+        arr = (B.ptrig_desc * 1)(d)
+        assert lib.ptrig_batch_plan_create(ctypes.byref(h), arr, 1, 0) == 1
+        assert not h.value
+    arr = (B.ptrig_desc * 1)(B.ptrig_desc(1024, 2048, 0, 10, 0, 0))
+    assert lib.ptrig_batch_plan_create(ctypes.byref(h), arr, 1, 8) == 1  # unknown flag
+    assert lib.ptrig_batch_plan_create(None, arr, 1, 0) == 1
+    assert lib.ptrig_batch_plan_create(ctypes.byref(h), None, 3, 0) == 1
+    lib.ptrig_batch_plan_destroy(None)
+
+
+def test_product_path_does_not_reference_the_oracle():
+    """The package never imports, loads or runs anything under oracle/."""
+    pkg = os.path.join(ROOT, "paper_2502_10831_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                src = open(os.path.join(dirpath, f)).read()
+                for pat in (r"\bimport\s+oracle", r"\bfrom\s+oracle\b", r"ptrig_oracle", r"ptro_"):
+                    assert not re.search(pat, src), (f, pat)

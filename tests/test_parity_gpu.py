@@ -1,0 +1,393 @@
+"""GPU parity of libptrig against the FP64 oracle (element by element), through
+the C ABI.  Needs a CUDA GPU; run with -m gpu."""
+import math
+
+import numpy as np
+import pytest
+
+import parity as P
+from paper_2502_10831_gb300 import workloads
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+FUNCS = ("sin", "cos", "tan")
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2502_10831_gb300 import binding, build
+    build.build()
+    return binding
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _run(B, func, x_np, dtype="f32"):
+    x = _dev(x_np)
+    y = torch.empty_like(x)
+    getattr(B, f"ptrig_{func}_{dtype}")(x, y)
+    torch.cuda.synchronize()
+    return y.cpu().numpy()
+
+
+def _segments(B, x_np):
+    x = _dev(x_np.astype(np.float32))
+    s = torch.empty(x.shape, dtype=torch.uint8, device="cuda")
+    B.ptrig_segment_f32(x, s)
+    torch.cuda.synchronize()
+    return s.cpu().numpy()
+
+
+# ----------------------------------------------------------------- FP32 core
+
+
+@pytest.fixture(scope="module")
+def c1():
+    return workloads.parity(1 << 20)
+
+
+@pytest.mark.parametrize("func", FUNCS)
+def test_f32_parity_parity_workload(B, oracle, c1, func):
+    xd = c1.astype(np.float64)
+    y = _run(B, func, c1)
+    ref, _ = P.reference_with_gpu_segments(oracle, func, xd, _segments(B, c1))
+    P.check_values(oracle, func, xd, y, ref)
+
+
+def test_sincos_equals_sin_and_cos(B, c1):
+    x = _dev(c1)
+    s = torch.empty_like(x)
+    c = torch.empty_like(x)
+    B.ptrig_sincos_f32(x, s, c)
+    s1 = _run(B, "sin", c1)
+    c1v = _run(B, "cos", c1)
+    torch.cuda.synchronize()
+    assert np.array_equal(s.cpu().numpy(), s1) and np.array_equal(c.cpu().numpy(), c1v)
+
+
+def test_segment_indices_bit_exact_away_from_nodes(B, oracle, c1):
+    extra = workloads.bandwidth(1 << 18)
+    x = np.concatenate([c1, extra])
+    seg = _segments(B, x)
+    u, q, neg, seg_o, _ = oracle.reduce(x.astype(np.float64))
+    same = (seg & 0x0F) == seg_o
+    assert np.all(same | P.near_node(u))
+    assert np.array_equal(seg >> 4, q)
+    # the near-node share of the node-heavy workload is small but not empty
+    assert (~same).sum() < 0.01 * x.size
+
+
+def test_edge_values(B, oracle):
+    x = workloads.edge_values()
+    xd = x.astype(np.float64)
+    seg = _segments(B, x)
+    for func in FUNCS:
+        y = _run(B, func, x)
+        ref, _ = P.reference_with_gpu_segments(oracle, func, xd, seg)
+        P.check_values(oracle, func, xd, y, ref)
+        z = np.array([0.0, -0.0], dtype=np.float32)
+        yz = _run(B, func, z)
+        if func == "cos":
+            assert np.all(yz == 1.0)
+        else:
+            assert np.all(yz == 0.0) and list(np.signbit(yz)) == [False, True]
+
+
+@pytest.mark.parametrize("func", ("sin", "tan"))
+def test_large_arguments(B, oracle, func):
+    """|x| log-uniform in [1, 1e5] (FP64 Cody-Waite side path above 2^10 pi)
+    plus Payne-Hanek magnitudes up to the largest float."""
+    big = workloads.large(1 << 20)
+    r = np.random.default_rng(4)
+    huge = (10.0 ** r.uniform(9.5, 38.5, 4096) * r.choice([-1, 1], 4096)).astype(np.float32)
+    x = np.concatenate([big, huge[np.isfinite(huge)]])
+    xd = x.astype(np.float64)
+    y = _run(B, func, x)
+    ref, _ = P.reference_with_gpu_segments(oracle, func, xd, _segments(B, x))
+    P.check_values(oracle, func, xd, y, ref)
+
+
+# ------------------------------------------------- sizes, alignment, in place
+
+
+@pytest.mark.parametrize("offset", [0, 1, 2, 3])
+def test_sizes_alignment_and_guard_bands(B, oracle, offset):
+    sizes = [0, 1, 2, 3, 4, 5, 7, 8, 9, 15, 16, 17, 31, 33, 1000, 4099, 70001]
+    base = workloads.parity(80000)
+    canary = np.float32(-7777.5)
+    for n in sizes:
+        for func in ("sin", "tan", "sincos"):
+            pad = 64
+            xbuf = np.full(n + 2 * pad, np.float32(0.25), dtype=np.float32)
+            xbuf[pad + offset: pad + offset + n] = base[:n]
+            xb = _dev(xbuf)
+            yb = _dev(np.full(n + 2 * pad, canary, dtype=np.float32))
+            zb = _dev(np.full(n + 2 * pad, canary, dtype=np.float32))
+            xs = xb[pad + offset: pad + offset + n]
+            ys = yb[pad + offset: pad + offset + n]
+            zs = zb[pad + offset: pad + offset + n]
+            if func == "sincos":
+                B.ptrig_sincos_f32(xs, ys, zs, n)
+            else:
+                getattr(B, f"ptrig_{func}_f32")(xs, ys, n)
+            torch.cuda.synchronize()
+            yh = yb.cpu().numpy()
+            zh = zb.cpu().numpy()
+            lo, hi = pad + offset, pad + offset + n
+            assert np.all(yh[:lo] == canary) and np.all(yh[hi:] == canary)
+            if func != "sincos":
+                assert np.all(zh == canary)
+            else:
+                assert np.all(zh[:lo] == canary) and np.all(zh[hi:] == canary)
+            if n:
+                f0 = "sin" if func == "sincos" else func
+                ref = _run(B, f0, base[:n].copy())  # aligned, vector path
+                assert np.array_equal(yh[lo:hi], ref), (n, offset, func)
+                if func == "sincos":
+                    assert np.array_equal(zh[lo:hi], _run(B, "cos", base[:n].copy()))
+
+
+def test_in_place(B):
+    x = workloads.parity(10007)
+    for func in FUNCS:
+        t = _dev(x)
+        getattr(B, f"ptrig_{func}_f32")(t, t)
+        torch.cuda.synchronize()
+        assert np.array_equal(t.cpu().numpy(), _run(B, func, x))
+
+
+# ------------------------------------------------------------------ Taylor
+
+
+@pytest.mark.parametrize("nterms", [5, 7, 9])
+@pytest.mark.parametrize("func", FUNCS)
+def test_taylor_parity(B, oracle, func, nterms):
+    x = workloads.parity(1 << 18)
+    xd = x.astype(np.float64)
+    xt = _dev(x)
+    y = torch.empty_like(xt)
+    if nterms == 5:
+        getattr(B, f"ptrig_taylor_{func}_f32")(xt, y)
+    else:
+        B.ptrig_taylor_n_f32(FUNCS.index(func), nterms, xt, y)
+    torch.cuda.synchronize()
+    yh = y.cpu().numpy().astype(np.float64)
+    ref = oracle.taylor(func, nterms, xd)
+    if func == "tan":
+        rel = np.abs(yh - ref) / np.maximum(np.abs(ref), 1e-30)
+        assert rel.max() <= 1e-5
+    else:
+        assert np.abs(yh - ref).max() <= 1e-6
+
+
+# --------------------------------------------------------------- derivatives
+
+
+@pytest.mark.parametrize("func", FUNCS)
+def test_bwd_f32_parity(B, oracle, func):
+    x = workloads.parity(1 << 18)
+    xd = x.astype(np.float64)
+    g = np.random.default_rng(9).standard_normal(x.size).astype(np.float32)
+    xt, gt = _dev(x), _dev(g)
+    gx = torch.empty_like(xt)
+    getattr(B, f"ptrig_{func}_bwd_f32")(xt, gt, gx)
+    torch.cuda.synchronize()
+    got = gx.cpu().numpy().astype(np.float64)
+    u, *_ = oracle.reduce(xd)
+    keep = ~P.near_node(u)
+    if func == "tan":
+        keep &= np.abs(oracle.proposed("cos", xd)) >= 1e-3
+    ref = g.astype(np.float64) * oracle.derivative(func, xd)
+    err = np.abs(got - ref)[keep] / np.maximum(1.0, np.abs(ref[keep]))
+    assert err.max() <= 2e-5, err.max()
+
+
+@pytest.mark.parametrize("func", FUNCS)
+def test_f64_forward_and_derivative(B, oracle, func):
+    r = np.random.default_rng(21)
+    x = np.concatenate([workloads.parity(1 << 16).astype(np.float64), r.uniform(-1e6, 1e6, 1 << 14),
+                        10.0 ** r.uniform(9, 300, 2048), [0.0, -0.0, math.pi / 2, 1e-300]])
+    xt = _dev(x)
+    y = torch.empty_like(xt)
+    getattr(B, f"ptrig_{func}_f64")(xt, y)
+    g = torch.ones_like(xt)
+    dy = torch.empty_like(xt)
+    getattr(B, f"ptrig_{func}_bwd_f64")(xt, g, dy)
+    torch.cuda.synchronize()
+    yh, dyh = y.cpu().numpy(), dy.cpu().numpy()
+    u, *_ = oracle.reduce(x)
+    nn = np.abs(u - np.round(u / P.STEP) * P.STEP) < 1e-13
+    ref = oracle.proposed(func, x)
+    dref = oracle.derivative(func, x)
+    keep = ~nn
+    if func == "tan":
+        keep &= np.abs(oracle.proposed("cos", x)) >= 1e-3
+        assert np.max(np.abs(yh - ref)[keep] / np.abs(ref[keep])) <= 1e-11
+    else:
+        assert np.max(np.abs(yh - ref)[keep]) <= 1e-12
+    assert np.max(np.abs(dyh - dref)[keep] / np.maximum(1.0, np.abs(dref[keep]))) <= 1e-10
+
+
+# ---------------------------------------------------------------- f16 / bf16
+
+
+def _half_ref_tol(func, dt):
+    if func in ("sin", "cos"):
+        return 2e-3
+    return 2.0 ** -11 + 1e-6 if dt == "f16" else 2.0 ** -8 + 1e-6
+
+
+@pytest.mark.parametrize("dt", ["f16", "bf16"])
+@pytest.mark.parametrize("func", ("sin", "cos", "tan", "sincos"))
+def test_half_parity(B, oracle, func, dt):
+    n = 1 << 20
+    if dt == "f16":
+        xh = workloads.half16(n)
+        bits = xh.view(np.uint16)
+        xd = xh.astype(np.float64)
+    else:
+        bits = workloads.half_bf16(n)
+        xd = workloads.bf16_bits_to_f32(bits).astype(np.float64)
+    xt = _dev(bits.view(np.int16))
+    y0 = torch.empty_like(xt)
+    if func == "sincos":
+        y1 = torch.empty_like(xt)
+        getattr(B, f"ptrig_sincos_{dt}")(xt, y0, y1)
+        outs = {"sin": y0, "cos": y1}
+    else:
+        getattr(B, f"ptrig_{func}_{dt}")(xt, y0)
+        outs = {func: y0}
+    torch.cuda.synchronize()
+    seg = _segments(B, xd.astype(np.float32))
+    for f, t in outs.items():
+        raw = t.cpu().numpy().view(np.uint16)
+        got = raw.view(np.float16).astype(np.float64) if dt == "f16" else \
+            workloads.bf16_bits_to_f32(raw).astype(np.float64)
+        ref, _ = P.reference_with_gpu_segments(oracle, f, xd, seg)
+        tol = _half_ref_tol(f, dt)
+        if f in ("sin", "cos"):
+            assert np.abs(got - ref).max() <= tol, (f, dt, np.abs(got - ref).max())
+        else:
+            big = 65504.0 if dt == "f16" else 3.0e38
+            keep = (np.abs(oracle.proposed("cos", xd)) >= 1e-3) & (np.abs(ref) < 0.99 * big) & \
+                   (np.abs(ref) > 1e-4)
+            rel = np.abs(got[keep] - ref[keep]) / np.abs(ref[keep])
+            assert rel.max() <= tol, (dt, rel.max())
+
+
+# -------------------------------------------------------------------- batch
+
+
+def _make_batch(n_arrays=60, seed=3):
+    r = np.random.default_rng(seed)
+    lengths = list(r.integers(0, 20000, n_arrays)) + [0, 1, 3, 5, 4096, 65537]
+    funcs = list(r.integers(0, 4, len(lengths)))
+    offs = list(r.integers(0, 4, len(lengths)))
+    return lengths, funcs, offs
+
+
+def test_batch_matches_single_kernels_and_oracle(B, oracle):
+    lengths, funcs, offs = _make_batch()
+    xs, ys, zs, descs, keep = [], [], [], [], []
+    for i, (n, f, o) in enumerate(zip(lengths, funcs, offs)):
+        xh = workloads.batch_array(i, n)
+        xb = _dev(np.concatenate([np.zeros(o, np.float32), xh]))
+        yb = torch.full_like(xb, -5.0)
+        zb = torch.full_like(xb, -5.0)
+        x, y, z = xb[o:], yb[o:], zb[o:]
+        keep.append((xb, yb, zb))
+        xs.append(xh)
+        ys.append(y)
+        zs.append(z)
+        descs.append((x, y, z if f == 3 else None, n, f))
+    for flags in (0, B.BATCH_GRAPH):
+        for y in ys:
+            y.fill_(-5.0)
+        plan = B.BatchPlan(descs, flags)
+        plan.set_config(128, 8)
+        plan.run()
+        torch.cuda.synchronize()
+        for i, (n, f) in enumerate(zip(lengths, funcs)):
+            if n == 0:
+                continue
+            got = ys[i].cpu().numpy()[:n]
+            name = ("sin", "cos", "tan", "sin")[f]
+            assert np.array_equal(got, _run(B, name, xs[i])), (i, n, f)
+            if f == 3:
+                assert np.array_equal(zs[i].cpu().numpy()[:n], _run(B, "cos", xs[i]))
+            xd = xs[i].astype(np.float64)
+            ref, _ = P.reference_with_gpu_segments(oracle, name, xd, _segments(B, xs[i]))
+            P.check_values(oracle, name, xd, got, ref)
+        res = plan.autotune(reps=2, candidates=[(128, 8), (256, 16), (512, 4)])
+        assert res["block"] in (128, 256, 512)
+        plan.run()
+        plan.run_per_array()
+        torch.cuda.synchronize()
+        plan.close()
+
+
+# --------------------------------------------------------- full-size sample
+
+
+def test_full_size_bandwidth_workload_sampled(B, oracle):
+    """2^28 angles of the bandwidth workload in the benchmark's launch
+    configuration: a random sample of outputs against the oracle, and
+    sin^2 + cos^2 = 1 (up to FP32 rounding) at every element."""
+    n = 1 << 28
+    x = workloads.bandwidth(n)
+    xt = _dev(x)
+    s = torch.empty_like(xt)
+    c = torch.empty_like(xt)
+    t = torch.empty_like(xt)
+    B.ptrig_sincos_f32(xt, s, c)
+    B.ptrig_tan_f32(xt, t)
+    torch.cuda.synchronize()
+    dev = (s * s + c * c - 1).abs().max().item()
+    assert dev <= 2e-6
+    r = np.random.default_rng(17)
+    idx = np.unique(np.concatenate([r.integers(0, n, 1 << 16), np.arange(1000), np.arange(n - 1000, n)]))
+    xi = x[idx]
+    xd = xi.astype(np.float64)
+    seg = _segments(B, xi)
+    it = torch.from_numpy(idx).cuda()
+    for f, out in (("sin", s), ("cos", c), ("tan", t)):
+        got = out[it].cpu().numpy()
+        ref, _ = P.reference_with_gpu_segments(oracle, f, xd, seg)
+        P.check_values(oracle, f, xd, got, ref)
+    del xt, s, c, t
+    torch.cuda.empty_cache()
+
+
+# ------------------------------------------------------------ misc behaviour
+
+
+def test_cuda_math_comparison_kernels(B):
+    x = workloads.parity(1 << 16)
+    xt = _dev(x)
+    for fast in (0, 1):
+        for fi, f in enumerate(FUNCS):
+            y = torch.empty_like(xt)
+            B.ptrig_cudamath_f32(fi, fast, xt, y)
+            torch.cuda.synchronize()
+            ref = getattr(np, f)(x.astype(np.float64))
+            err = np.abs(y.cpu().numpy() - ref)
+            if f == "tan":
+                err = err / np.maximum(1.0, np.abs(ref))
+            assert err.max() < (1e-5 if not fast else 2e-2)
+
+
+def test_errors_on_gpu(B):
+    from paper_2502_10831_gb300.binding import PtrigError
+    x = torch.zeros(16, device="cuda")
+    with pytest.raises(PtrigError):
+        B.ptrig_sincos_f32(x, x, None)
+    with pytest.raises(PtrigError):
+        B.ptrig_taylor_n_f32(1, 4, x, x)
+    B.ptrig_sin_f32(x, x, 0)  # n == 0 is a no-op
+    assert B.ptrig_version() >= 10000
