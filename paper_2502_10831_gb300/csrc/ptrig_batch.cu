@@ -34,8 +34,42 @@ namespace ptrig {
 
 static_assert(sizeof(ptrig_desc) == 40, "ptrig_desc layout");
 
+// Vectors v, v + blockDim, ... < nv of one tile with the full reduction (out
+// of line; reached only when the tile holds an angle beyond 2^10 pi).
 template <int OP>
-__device__ __forceinline__ void batch_tile(const ptrig_desc &d, uint64_t start, uint32_t len, const float4 *tab) {
+static __device__ __noinline__ void batch_resume_full(const float *x, float *y0, float *y1, uint32_t v,
+                                                      uint32_t nv, const float4 *tab) {
+  using F = Proposed<OP>;
+  for (; v < nv; v += blockDim.x) {
+    float f[4], o0[4], o1[4];
+    Storage<float>::unpack(ld_stream(reinterpret_cast<const uint4 *>(x) + v), f);
+    for (int e = 0; e < 4; ++e) F::template eval<true>(f[e], tab, o0[e], o1[e]);
+    st_stream(reinterpret_cast<uint4 *>(y0) + v, Storage<float>::pack(o0));
+    if constexpr (F::NOUT == 2) st_stream(reinterpret_cast<uint4 *>(y1) + v, Storage<float>::pack(o1));
+  }
+}
+
+// Elements [from, len) of a tile one at a time (unaligned arrays, n % 4 tails);
+// out of line like the full-reduction path.
+template <int OP>
+static __device__ __noinline__ void batch_elements(const float *x, float *y0, float *y1, uint32_t from,
+                                                   uint32_t len, const float4 *tab) {
+  using F = Proposed<OP>;
+  for (uint32_t i = from + threadIdx.x; i < len; i += blockDim.x) {
+    float o0, o1;
+    F::template eval<true>(__ldg(x + i), tab, o0, o1);
+    y0[i] = o0;
+    if constexpr (F::NOUT == 2) y1[i] = o1;
+  }
+}
+
+// One tile (len elements from `start` of array d).  Vector path when the
+// tile's pointers are 16-byte aligned: each thread issues up to four loads,
+// then computes one vector at a time; element path otherwise and for the
+// n % 4 tail.
+template <int OP>
+static __device__ __noinline__ void batch_tile(const ptrig_desc d, uint64_t start, uint32_t len,
+                                               const float4 *tab) {
   using F = Proposed<OP>;
   const float *x = d.x + start;
   float *y0 = d.y0 + start;
@@ -44,39 +78,34 @@ __device__ __forceinline__ void batch_tile(const ptrig_desc &d, uint64_t start, 
   if (OP == OP_SINCOS) a |= (uintptr_t)y1;
   uint32_t done = 0;
   if ((a & 15u) == 0) {
-    constexpr int U = 2;  // vectors in flight per thread
+    constexpr int U = 4;
     const uint32_t nv = len / 4;
+    const uint4 *xv = reinterpret_cast<const uint4 *>(x);
+    uint32_t resume = 0;
     for (uint32_t v0 = threadIdx.x; v0 < nv; v0 += blockDim.x * U) {
-      uint4 in[U];
+      uint4 buf[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const uint32_t i = v0 + u * blockDim.x;
-        if (i < nv) in[u] = ld_stream(reinterpret_cast<const uint4 *>(x) + i);
+        if (i < nv) buf[u] = ld_stream(xv + i);
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const uint32_t i = v0 + u * blockDim.x;
-        if (i < nv) {
-          float f[4], o0[4], o1[4];
-          Storage<float>::unpack(in[u], f);
-#pragma unroll
-          for (int e = 0; e < 4; ++e) F::eval(f[e], tab, o0[e], o1[e]);
-          st_stream(reinterpret_cast<uint4 *>(y0) + i, Storage<float>::pack(o0));
-          if constexpr (F::NOUT == 2) st_stream(reinterpret_cast<uint4 *>(y1) + i, Storage<float>::pack(o1));
+        if (i < nv && !map_vector_fast<float, F>(buf[u], i, y0, y1, tab)) {
+          resume = i + 1;
+          goto full;
         }
       }
     }
+  full:
+    if (resume) batch_resume_full<OP>(x, y0, y1, resume - 1, nv, tab);
     done = nv * 4;
   }
-  for (uint32_t i = done + threadIdx.x; i < len; i += blockDim.x) {
-    float o0, o1;
-    F::eval(__ldg(x + i), tab, o0, o1);
-    y0[i] = o0;
-    if constexpr (F::NOUT == 2) y1[i] = o1;
-  }
+  if (done < len) batch_elements<OP>(x, y0, y1, done, len, tab);
 }
 
-__global__ void __launch_bounds__(512) k_batch(const ptrig_desc *__restrict__ descs,
+__global__ void __launch_bounds__(512, 2) k_batch(const ptrig_desc *__restrict__ descs,
                                                const uint32_t *__restrict__ owner,
                                                const uint64_t *__restrict__ first_tile, uint64_t ntiles,
                                                uint32_t tile_elems) {

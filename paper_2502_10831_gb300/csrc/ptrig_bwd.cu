@@ -4,41 +4,111 @@
 
 namespace ptrig {
 
-template <int OP, int VPT>
+// One vector pair with the FP32 reduction; false (nothing stored) when an
+// angle lies outside the FP32 reduction range or is NaN / inf.
+template <int OP>
+__device__ __forceinline__ bool bwd_vector_fast(uint4 xv, uint4 gv, size_t i, float *gx, const float4 *tab) {
+  float f[4], g[4], o[4];
+  Storage<float>::unpack(xv, f);
+  bool slow = false;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) slow |= needs_slow(f[e]);
+  if (slow) return false;
+  Storage<float>::unpack(gv, g);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) o[e] = __fmul_rn(g[e], Deriv<OP>::template eval<false>(f[e], tab));
+  st_stream(reinterpret_cast<uint4 *>(gx) + i, Storage<float>::pack(o));
+  return true;
+}
+
+// Remaining vectors of a thread with the full reduction (out of line).
+template <int OP>
+static __device__ __noinline__ void bwd_resume_full(const float *__restrict__ x, const float *gy, float *gx,
+                                                    size_t i, size_t nvec, size_t stride, const float4 *tab) {
+  for (; i < nvec; i += stride) {
+    float f[4], g[4], o[4];
+    Storage<float>::unpack(ld_stream(reinterpret_cast<const uint4 *>(x) + i), f);
+    Storage<float>::unpack(*(reinterpret_cast<const uint4 *>(gy) + i), g);
+    for (int e = 0; e < 4; ++e) o[e] = __fmul_rn(g[e], Deriv<OP>::template eval<true>(f[e], tab));
+    st_stream(reinterpret_cast<uint4 *>(gx) + i, Storage<float>::pack(o));
+  }
+}
+
+// Same software-pipelined structure (and the same persistent / one-shot
+// modes) as k_map, with a ring of D (x, gy) vector pairs per thread.
+template <int OP, int D, bool PERSIST>
 __global__ void __launch_bounds__(512) k_bwd(const float *__restrict__ x, const float *gy, float *gx, size_t n) {
   __shared__ float4 s_tab[8];
   if (threadIdx.x < 8) s_tab[threadIdx.x] = c_tab_f32[threadIdx.x];
   __syncthreads();
   const size_t nvec = n / 4;
-  const size_t step = (size_t)blockDim.x * VPT;
-  const size_t stride = step * gridDim.x;
-  for (size_t base = (size_t)blockIdx.x * step + threadIdx.x; base < nvec; base += stride) {
-    uint4 xin[VPT], gin[VPT];
-#pragma unroll
-    for (int v = 0; v < VPT; ++v) {
-      const size_t i = base + (size_t)v * blockDim.x;
-      if (i < nvec) {
-        xin[v] = ld_stream(reinterpret_cast<const uint4 *>(x) + i);
-        gin[v] = *(reinterpret_cast<const uint4 *>(gy) + i);
-      }
+  if (blockIdx.x == 0) {
+    for (size_t k = nvec * 4 + threadIdx.x; k < n; k += blockDim.x) {
+      gx[k] = __fmul_rn(gy[k], Deriv<OP>::template eval<true>(x[k], s_tab));
     }
+  }
+  size_t i, step, end;
+  if (PERSIST) {
+    i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    step = (size_t)gridDim.x * blockDim.x;
+    end = nvec;
+  } else {
+    const size_t chunk = (size_t)blockIdx.x * blockDim.x * D;
+    i = chunk + threadIdx.x;
+    step = blockDim.x;
+    end = chunk + (size_t)blockDim.x * D;
+    if (end > nvec) end = nvec;
+  }
+  const uint4 *xv = reinterpret_cast<const uint4 *>(x);
+  const uint4 *gv = reinterpret_cast<const uint4 *>(gy);
+  size_t resume = 0;
+  uint4 bx[D], bg[D];
 #pragma unroll
-    for (int v = 0; v < VPT; ++v) {
-      const size_t i = base + (size_t)v * blockDim.x;
-      if (i < nvec) {
-        float f[4], g[4], o[4];
-        Storage<float>::unpack(xin[v], f);
-        Storage<float>::unpack(gin[v], g);
+  for (int d = 0; d < D; ++d) {
+    const size_t j = i + (size_t)d * step;
+    if (j < end) {
+      bx[d] = ld_stream(xv + j);
+      bg[d] = gv[j];
+    }
+  }
+  for (; i < end; i += (size_t)D * step) {
 #pragma unroll
-        for (int e = 0; e < 4; ++e) o[e] = __fmul_rn(g[e], Deriv<OP>::eval(f[e], s_tab));
-        st_stream(reinterpret_cast<uint4 *>(gx) + i, Storage<float>::pack(o));
+    for (int d = 0; d < D; ++d) {
+      const size_t ii = i + (size_t)d * step;
+      if (ii < end) {
+        const uint4 cx = bx[d], cg = bg[d];
+        if (PERSIST) {
+          const size_t jn = ii + (size_t)D * step;
+          if (jn < end) {
+            bx[d] = ld_stream(xv + jn);
+            bg[d] = gv[jn];
+          }
+        }
+        if (!bwd_vector_fast<OP>(cx, cg, ii, gx, s_tab)) {
+          resume = ii + 1;
+          goto full;
+        }
       }
     }
   }
-  if (blockIdx.x == 0) {
-    for (size_t i = nvec * 4 + threadIdx.x; i < n; i += blockDim.x) {
-      gx[i] = __fmul_rn(gy[i], Deriv<OP>::eval(x[i], s_tab));
-    }
+  return;
+full:
+  bwd_resume_full<OP>(x, gy, gx, resume - 1, end, step, s_tab);
+}
+
+template <int OP, int D>
+static void launch_bwd_d(const LaunchCfg &c, int sms, const float *x, const float *gy, float *gx, size_t n,
+                         cudaStream_t s) {
+  const size_t nvec = n / 4;
+  if (c.blocks_per_sm > 0) {
+    size_t g = (nvec + c.block - 1) / c.block;
+    const size_t cap = (size_t)sms * (size_t)c.blocks_per_sm;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    k_bwd<OP, D, true><<<(unsigned)g, c.block, 0, s>>>(x, gy, gx, n);
+  } else {
+    const size_t g = grid_for(nvec, (size_t)c.block * D, LaunchCfg{c.block, D, 0}, sms);
+    k_bwd<OP, D, false><<<(unsigned)g, c.block, 0, s>>>(x, gy, gx, n);
   }
 }
 
@@ -49,7 +119,7 @@ __global__ void __launch_bounds__(512) k_bwd_scalar(const float *__restrict__ x,
   if (threadIdx.x < 8) s_tab[threadIdx.x] = c_tab_f32[threadIdx.x];
   __syncthreads();
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)blockDim.x * gridDim.x) {
-    gx[i] = __fmul_rn(gy[i], Deriv<OP>::eval(x[i], s_tab));
+    gx[i] = __fmul_rn(gy[i], Deriv<OP>::template eval<true>(x[i], s_tab));
   }
 }
 
@@ -63,16 +133,15 @@ static ptrig_status launch_bwd_op(const float *x, const float *gy, float *gx, si
     k_bwd_scalar<OP><<<(unsigned)blocks, c.block, 0, s>>>(x, gy, gx, n);
     return finish_launch();
   }
-  const size_t blocks = grid_for(n / 4, (size_t)c.block * c.vpt, c, sms);
   switch (c.vpt) {
     case 1:
-      k_bwd<OP, 1><<<(unsigned)blocks, c.block, 0, s>>>(x, gy, gx, n);
+      launch_bwd_d<OP, 1>(c, sms, x, gy, gx, n, s);
       break;
     case 2:
-      k_bwd<OP, 2><<<(unsigned)blocks, c.block, 0, s>>>(x, gy, gx, n);
+      launch_bwd_d<OP, 2>(c, sms, x, gy, gx, n, s);
       break;
     default:
-      k_bwd<OP, 4><<<(unsigned)blocks, c.block, 0, s>>>(x, gy, gx, n);
+      launch_bwd_d<OP, 4>(c, sms, x, gy, gx, n, s);
       break;
   }
   return finish_launch();

@@ -85,6 +85,23 @@ __device__ __forceinline__ RedF reduce_fast(float x) {
   return {r, __float_as_uint(y)};
 }
 
+// Two angles at once with packed FP32 (FFMA2 / FADD2): the same roundings,
+// lane by lane, as reduce_fast().
+struct RedF2 {
+  float2 r;
+  uint32_t jb0, jb1;
+};
+
+__device__ __forceinline__ RedF2 reduce_fast2(float2 x) {
+  const float2 y = __ffma2_rn(x, make_float2(PTRIG_2_OVER_PI_F, PTRIG_2_OVER_PI_F),
+                              make_float2(PTRIG_RINT_MAGIC_F, PTRIG_RINT_MAGIC_F));
+  const float2 jf = __fadd2_rn(y, make_float2(-PTRIG_RINT_MAGIC_F, -PTRIG_RINT_MAGIC_F));
+  float2 r = __ffma2_rn(jf, make_float2(-PTRIG_PIO2_F1, -PTRIG_PIO2_F1), x);
+  r = __ffma2_rn(jf, make_float2(-PTRIG_PIO2_F2, -PTRIG_PIO2_F2), r);
+  r = __ffma2_rn(jf, make_float2(-PTRIG_PIO2_F3, -PTRIG_PIO2_F3), r);
+  return {r, __float_as_uint(y.x), __float_as_uint(y.y)};
+}
+
 // Bits [lo, lo + 64) of a little-endian 8-limb integer (0 <= lo <= 192).
 __device__ __forceinline__ uint64_t bits64(const uint32_t (&z)[8], int lo) {
   const int w = lo >> 5, s = lo & 31;
@@ -221,11 +238,63 @@ __device__ __forceinline__ uint32_t table_index(float t, uint32_t jb) {
   return ((jb & 1u) << 2) | ((uint32_t)kq & 3u);
 }
 
+// Two angles of the fast range at once: packed FP32 for the reduction, the
+// segment scaling, h^2 and the final products; table lookup, MUFU and signs
+// per lane.  Bit-identical to two calls of Proposed<OP>::eval<false>.
+template <int OP>
+__device__ __forceinline__ void proposed_pair(float2 x, const float4 *tab, float2 &o0, float2 &o1) {
+  const RedF2 red = reduce_fast2(x);
+  const float2 t = make_float2(fabsf(red.r.x), fabsf(red.r.y));
+  const float2 v = __fmul2_rn(t, make_float2(PTRIG_12_OVER_PI_F, PTRIG_12_OVER_PI_F));
+  const uint32_t i0 = ((red.jb0 & 1u) << 2) | ((uint32_t)__float2int_rd(v.x) & 3u);
+  const uint32_t i1 = ((red.jb1 & 1u) << 2) | ((uint32_t)__float2int_rd(v.y) & 3u);
+  const float4 c0 = tab[i0];
+  const float4 c1 = tab[i1];
+  const float2 N = make_float2(__fmaf_rn(c0.x, t.x, c0.y), __fmaf_rn(c1.x, t.y, c1.y));
+  const float2 D = make_float2(__fmaf_rn(c0.z, t.x, c0.w), __fmaf_rn(c1.z, t.y, c1.w));
+  const Signs g0 = sign_bits(red.jb0, __float_as_uint(red.r.x));
+  const Signs g1 = sign_bits(red.jb1, __float_as_uint(red.r.y));
+  if (OP == OP_TAN) {
+    const float2 q = __fmul2_rn(N, make_float2(rcp_approx(D.x), rcp_approx(D.y)));
+    o0 = make_float2(xor_sign(q.x, g0.t), xor_sign(q.y, g1.t));
+  } else {
+    const float2 h2 = __ffma2_rn(N, N, __fmul2_rn(D, D));
+    const float2 rs = make_float2(rsqrt_approx(h2.x), rsqrt_approx(h2.y));
+    if (OP == OP_SIN || OP == OP_SINCOS) {
+      const float2 sv = __fmul2_rn(N, rs);
+      o0 = make_float2(xor_sign(sv.x, g0.s), xor_sign(sv.y, g1.s));
+    }
+    if (OP == OP_COS || OP == OP_SINCOS) {
+      const float2 cv = __fmul2_rn(D, rs);
+      const float2 c = make_float2(xor_sign(cv.x, g0.c), xor_sign(cv.y, g1.c));
+      if (OP == OP_COS)
+        o0 = c;
+      else
+        o1 = c;
+    }
+  }
+}
+
+// FULL = false: the caller guarantees |x| <= 2^10 pi (FP32 reduction only).
+template <bool FULL>
+__device__ __forceinline__ RedF reduce_sel(float x) {
+  return FULL ? reduce_f32(x) : reduce_fast(x);
+}
+
+// True if x needs the FP64 / Payne-Hanek side path (or is NaN / infinite).
+__device__ __forceinline__ bool needs_slow(float x) { return !(fabsf(x) <= PTRIG_FAST_LIMIT_F); }
+
 template <int OP>
 struct Proposed {
   static constexpr int NOUT = (OP == OP_SINCOS) ? 2 : 1;
+  static constexpr bool HAS_SLOW = true;
+  static constexpr bool HAS_PAIR = true;
+  __device__ __forceinline__ static void eval_pair(float2 x, const float4 *tab, float2 &o0, float2 &o1) {
+    proposed_pair<OP>(x, tab, o0, o1);
+  }
+  template <bool FULL = true>
   __device__ __forceinline__ static void eval(float x, const float4 *tab, float &o0, float &o1) {
-    const RedF red = reduce_f32(x);
+    const RedF red = reduce_sel<FULL>(x);
     const float t = fabsf(red.r);
     const float4 c = tab[table_index(t, red.jb)];
     const float N = __fmaf_rn(c.x, t, c.y);
@@ -260,8 +329,12 @@ __device__ __forceinline__ constexpr float taylor_coef(int i) {
 template <int OP, int NT>
 struct Taylor {
   static constexpr int NOUT = 1;
+  static constexpr bool HAS_SLOW = true;
+  static constexpr bool HAS_PAIR = false;
+  __device__ __forceinline__ static void eval_pair(float2, const float4 *, float2 &, float2 &) {}
+  template <bool FULL = true>
   __device__ __forceinline__ static void eval(float x, const float4 *, float &o0, float &) {
-    const RedF red = reduce_f32(x);
+    const RedF red = reduce_sel<FULL>(x);
     const float t = fabsf(red.r);
     const float u = (red.jb & 1u) ? __fsub_rn(PTRIG_PIO2_F, t) : t;
     const float u2 = __fmul_rn(u, u);
@@ -284,8 +357,9 @@ struct Taylor {
 //   d(N/D)/dt = Delta_t / D^2, d(N/h)/dt = D Delta_t / h^3, d(D/h)/dt = -N Delta_t / h^3.
 template <int OP>
 struct Deriv {
+  template <bool FULL = true>
   __device__ __forceinline__ static float eval(float x, const float4 *tab) {
-    const RedF red = reduce_f32(x);
+    const RedF red = reduce_sel<FULL>(x);
     const float t = fabsf(red.r);
     const float4 c = tab[table_index(t, red.jb)];
     const float N = __fmaf_rn(c.x, t, c.y);

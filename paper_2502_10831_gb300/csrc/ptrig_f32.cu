@@ -52,6 +52,10 @@ ptrig_status launch_taylor_f32(int op, int nterms, const float *x, float *y, siz
 template <int OP, int FAST>
 struct CudaMath {
   static constexpr int NOUT = (OP == OP_SINCOS) ? 2 : 1;
+  static constexpr bool HAS_SLOW = false;
+  static constexpr bool HAS_PAIR = false;
+  __device__ __forceinline__ static void eval_pair(float2, const float4 *, float2 &, float2 &) {}
+  template <bool FULL = true>
   __device__ __forceinline__ static void eval(float x, const float4 *, float &o0, float &o1) {
     if (FAST) {
       if (OP == OP_SIN) o0 = __sinf(x);

@@ -13,12 +13,13 @@ namespace ptrig {
 
 struct LaunchCfg {
   int block;          // threads per block
-  int vpt;            // 16-byte vectors per thread per iteration (1, 2, 4)
-  int blocks_per_sm;  // grid cap in blocks per SM, 0 = uncapped
+  int vpt;            // 16-byte loads kept in flight per thread (1, 2, 4)
+  int blocks_per_sm;  // > 0: persistent grid of this many blocks per SM; 0: one-shot chunks
 };
 
 LaunchCfg get_cfg(int family);
 int sm_count();                       // SMs of the current device, <= 0 if none
+int occupancy(const void *kernel, int block);  // resident blocks per SM (cached)
 ptrig_status finish_launch();         // checks the launch, records CUDA errors
 ptrig_status cuda_fail(cudaError_t e);  // records e, returns PTRIG_ERR_CUDA
 

@@ -1,9 +1,8 @@
 // ptrig_map.cuh -- streaming elementwise kernels and their launch helper.
 //
-// Each thread moves VPT 16-byte vectors per iteration (loads for all of them
-// issued before any arithmetic), reads with ld.global.nc.L1::no_allocate and
-// writes with st.global.cs: every byte is touched once, so nothing is kept in
-// L1 and the stores are marked evict-first in L2.  The eight-entry coefficient
+// Reads use ld.global.nc.L1::no_allocate and writes st.global.cs: every byte is
+// touched once, so nothing is kept in L1 and the stores are marked
+// evict-first in L2.  The eight-entry coefficient
 // table is staged in shared memory; its 128 bytes occupy all 32 banks once,
 // so a warp's LDS.128 lookups never conflict.
 #pragma once
@@ -15,7 +14,73 @@
 
 namespace ptrig {
 
-template <typename T, class F, int VPT>
+// Evaluates and stores one 16-byte vector with the FP32 reduction.  Returns
+// false, storing nothing, when an element lies outside the FP32 reduction
+// range (or is NaN / inf); the caller then hands the rest of its work to the
+// full-reduction path.
+template <typename T, class F>
+__device__ __forceinline__ bool map_vector_fast(uint4 v, size_t i, T *y0, T *y1, const float4 *tab) {
+  using S = Storage<T>;
+  constexpr int E = S::EPV;
+  float f[E], o0[E], o1[E];
+  S::unpack(v, f);
+  if constexpr (F::HAS_SLOW) {
+    bool slow = false;
+#pragma unroll
+    for (int e = 0; e < E; ++e) slow |= needs_slow(f[e]);
+    if (slow) return false;
+  }
+  // packed FP32 pairs where the kernel is instruction-bound (16-bit storage:
+  // half the bytes per angle); FP32 storage is memory-bound and keeps the
+  // scalar form, which needs fewer registers
+  if constexpr (F::HAS_PAIR && sizeof(T) == 2) {
+#pragma unroll
+    for (int e = 0; e < E; e += 2) {
+      float2 a, b;
+      F::eval_pair(make_float2(f[e], f[e + 1]), tab, a, b);
+      o0[e] = a.x;
+      o0[e + 1] = a.y;
+      o1[e] = b.x;
+      o1[e + 1] = b.y;
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < E; ++e) F::template eval<false>(f[e], tab, o0[e], o1[e]);
+  }
+  st_stream(reinterpret_cast<uint4 *>(y0) + i, S::pack(o0));
+  if constexpr (F::NOUT == 2) st_stream(reinterpret_cast<uint4 *>(y1) + i, S::pack(o1));
+  return true;
+}
+
+// Vectors i, i + stride, ... < nvec with the full reduction (FP32 Cody-Waite,
+// FP64 Cody-Waite or Payne-Hanek per element).  Out of line and reached only
+// after a thread met an angle beyond 2^10 pi, so the pipelined loop carries no
+// call and no FP64 / Payne-Hanek register state.
+template <typename T, class F>
+static __device__ __noinline__ void map_resume_full(const T *__restrict__ x, T *__restrict__ y0,
+                                                    T *__restrict__ y1, size_t i, size_t nvec, size_t stride,
+                                                    const float4 *tab) {
+  using S = Storage<T>;
+  constexpr int E = S::EPV;
+  for (; i < nvec; i += stride) {
+    float f[E], o0[E], o1[E];
+    S::unpack(ld_stream(reinterpret_cast<const uint4 *>(x) + i), f);
+    for (int e = 0; e < E; ++e) F::template eval<true>(f[e], tab, o0[e], o1[e]);
+    st_stream(reinterpret_cast<uint4 *>(y0) + i, S::pack(o0));
+    if constexpr (F::NOUT == 2) st_stream(reinterpret_cast<uint4 *>(y1) + i, S::pack(o1));
+  }
+}
+
+// Software-pipelined stream of 16-byte vectors.  Thread t of block b handles
+// vectors base, base + step, ... below `end`, keeping a ring of D loads in
+// flight: the slot of the vector about to be computed is refilled with the
+// vector D steps ahead before the arithmetic starts.  One vector is computed
+// at a time, which keeps the loop at 52-64 registers.
+//   persistent (PERSIST = true):  base = b*B + t, step = grid*B, end = nvec;
+//     a grid of a few blocks per SM walks the whole array.
+//   one-shot   (PERSIST = false): base = b*B*D + t, step = B, end = base + D*B;
+//     each block streams one contiguous chunk of D*B vectors and retires.
+template <typename T, class F, int D, bool PERSIST>
 __global__ void __launch_bounds__(512) k_map(const T *__restrict__ x, T *__restrict__ y0, T *__restrict__ y1,
                                              size_t n) {
   __shared__ float4 s_tab[8];
@@ -24,37 +89,54 @@ __global__ void __launch_bounds__(512) k_map(const T *__restrict__ x, T *__restr
   using S = Storage<T>;
   constexpr int E = S::EPV;
   const size_t nvec = n / E;
-  const size_t step = (size_t)blockDim.x * VPT;
-  const size_t stride = step * gridDim.x;
-  const uint4 *xv = reinterpret_cast<const uint4 *>(x);
-  for (size_t base = (size_t)blockIdx.x * step + threadIdx.x; base < nvec; base += stride) {
-    uint4 in[VPT];
-#pragma unroll
-    for (int v = 0; v < VPT; ++v) {
-      const size_t i = base + (size_t)v * blockDim.x;
-      if (i < nvec) in[v] = ld_stream(xv + i);
+  if (blockIdx.x == 0) {  // the n % E elements after the last whole vector
+    for (size_t k = nvec * E + threadIdx.x; k < n; k += blockDim.x) {
+      float o0, o1;
+      F::template eval<true>(S::load1(x + k), s_tab, o0, o1);
+      S::store1(y0 + k, o0);
+      if constexpr (F::NOUT == 2) S::store1(y1 + k, o1);
     }
+  }
+  size_t i, step, end;
+  if (PERSIST) {
+    i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    step = (size_t)gridDim.x * blockDim.x;
+    end = nvec;
+  } else {
+    const size_t chunk = (size_t)blockIdx.x * blockDim.x * D;
+    i = chunk + threadIdx.x;
+    step = blockDim.x;
+    end = chunk + (size_t)blockDim.x * D;
+    if (end > nvec) end = nvec;
+  }
+  const uint4 *xv = reinterpret_cast<const uint4 *>(x);
+  size_t resume = 0;
+  uint4 buf[D];
 #pragma unroll
-    for (int v = 0; v < VPT; ++v) {
-      const size_t i = base + (size_t)v * blockDim.x;
-      if (i < nvec) {
-        float f[E], o0[E], o1[E];
-        S::unpack(in[v], f);
+  for (int d = 0; d < D; ++d) {
+    const size_t j = i + (size_t)d * step;
+    if (j < end) buf[d] = ld_stream(xv + j);
+  }
+  for (; i < end; i += (size_t)D * step) {
 #pragma unroll
-        for (int e = 0; e < E; ++e) F::eval(f[e], s_tab, o0[e], o1[e]);
-        st_stream(reinterpret_cast<uint4 *>(y0) + i, S::pack(o0));
-        if constexpr (F::NOUT == 2) st_stream(reinterpret_cast<uint4 *>(y1) + i, S::pack(o1));
+    for (int d = 0; d < D; ++d) {
+      const size_t ii = i + (size_t)d * step;
+      if (ii < end) {
+        const uint4 cur = buf[d];
+        if (PERSIST) {
+          const size_t jn = ii + (size_t)D * step;
+          if (jn < end) buf[d] = ld_stream(xv + jn);
+        }
+        if (!map_vector_fast<T, F>(cur, ii, y0, y1, s_tab)) {
+          resume = ii + 1;  // +1 so that 0 means "finished"
+          goto full;
+        }
       }
     }
   }
-  if (blockIdx.x == 0) {  // the n % E elements after the last whole vector
-    for (size_t i = nvec * E + threadIdx.x; i < n; i += blockDim.x) {
-      float o0, o1;
-      F::eval(S::load1(x + i), s_tab, o0, o1);
-      S::store1(y0 + i, o0);
-      if constexpr (F::NOUT == 2) S::store1(y1 + i, o1);
-    }
-  }
+  return;
+full:
+  map_resume_full<T, F>(x, y0, y1, resume - 1, end, step, s_tab);
 }
 
 // Any alignment: one element per thread per iteration.
@@ -67,7 +149,7 @@ __global__ void __launch_bounds__(512) k_map_scalar(const T *__restrict__ x, T *
   using S = Storage<T>;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)blockDim.x * gridDim.x) {
     float o0, o1;
-    F::eval(S::load1(x + i), s_tab, o0, o1);
+    F::template eval<true>(S::load1(x + i), s_tab, o0, o1);
     S::store1(y0 + i, o0);
     if constexpr (F::NOUT == 2) S::store1(y1 + i, o1);
   }
@@ -84,6 +166,22 @@ inline size_t grid_for(size_t units, size_t per_block, const LaunchCfg &c, int s
   return blocks;
 }
 
+template <typename T, class F, int D>
+ptrig_status launch_map_d(const LaunchCfg &c, int sms, const T *x, T *y0, T *y1, size_t n, cudaStream_t s) {
+  const size_t nvec = n / Storage<T>::EPV;
+  if (c.blocks_per_sm > 0) {  // persistent: blocks_per_sm resident blocks per SM
+    size_t g = (nvec + c.block - 1) / c.block;
+    const size_t cap = (size_t)sms * (size_t)c.blocks_per_sm;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    k_map<T, F, D, true><<<(unsigned)g, c.block, 0, s>>>(x, y0, y1, n);
+  } else {  // one-shot: one contiguous chunk of D * block vectors per block
+    const size_t g = grid_for(nvec, (size_t)c.block * D, LaunchCfg{c.block, D, 0}, sms);
+    k_map<T, F, D, false><<<(unsigned)g, c.block, 0, s>>>(x, y0, y1, n);
+  }
+  return finish_launch();
+}
+
 template <typename T, class F>
 ptrig_status launch_map(int family, const T *x, T *y0, T *y1, size_t n, cudaStream_t s) {
   const LaunchCfg c = get_cfg(family);
@@ -96,20 +194,14 @@ ptrig_status launch_map(int family, const T *x, T *y0, T *y1, size_t n, cudaStre
     k_map_scalar<T, F><<<(unsigned)blocks, c.block, 0, s>>>(x, y0, y1, n);
     return finish_launch();
   }
-  const size_t nvec = n / Storage<T>::EPV;
-  const size_t blocks = grid_for(nvec, (size_t)c.block * c.vpt, c, sms);
   switch (c.vpt) {
     case 1:
-      k_map<T, F, 1><<<(unsigned)blocks, c.block, 0, s>>>(x, y0, y1, n);
-      break;
+      return launch_map_d<T, F, 1>(c, sms, x, y0, y1, n, s);
     case 2:
-      k_map<T, F, 2><<<(unsigned)blocks, c.block, 0, s>>>(x, y0, y1, n);
-      break;
+      return launch_map_d<T, F, 2>(c, sms, x, y0, y1, n, s);
     default:
-      k_map<T, F, 4><<<(unsigned)blocks, c.block, 0, s>>>(x, y0, y1, n);
-      break;
+      return launch_map_d<T, F, 4>(c, sms, x, y0, y1, n, s);
   }
-  return finish_launch();
 }
 
 }  // namespace ptrig

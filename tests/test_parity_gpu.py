@@ -281,6 +281,31 @@ def test_half_parity(B, oracle, func, dt):
             assert rel.max() <= tol, (dt, rel.max())
 
 
+@pytest.mark.parametrize("dt", ["f16", "bf16"])
+def test_half_vector_and_scalar_paths_agree(B, dt):
+    """Aligned arrays take the 16-byte vector path (packed FP32 pairs);
+    misaligned ones and n % 8 tails the element path.  Both round alike."""
+    n = 40003
+    bits = workloads.half16(n).view(np.uint16) if dt == "f16" else workloads.half_bf16(n)
+    ref = {}
+    for off in range(0, 8):
+        buf = np.zeros(n + 16, dtype=np.uint16)
+        buf[off: off + n] = bits
+        xb = _dev(buf.view(np.int16))
+        ys = torch.zeros_like(xb)
+        yc = torch.zeros_like(xb)
+        getattr(B, f"ptrig_sincos_{dt}")(xb[off: off + n], ys[off: off + n], yc[off: off + n], n)
+        yt = torch.zeros_like(xb)
+        getattr(B, f"ptrig_tan_{dt}")(xb[off: off + n], yt[off: off + n], n)
+        torch.cuda.synchronize()
+        got = [t.cpu().numpy()[off: off + n] for t in (ys, yc, yt)]
+        if off == 0:
+            ref = got
+        else:
+            for g, r in zip(got, ref):
+                assert np.array_equal(g, r), (dt, off)
+
+
 # -------------------------------------------------------------------- batch
 
 
@@ -375,10 +400,13 @@ def test_cuda_math_comparison_kernels(B):
             y = torch.empty_like(xt)
             B.ptrig_cudamath_f32(fi, fast, xt, y)
             torch.cuda.synchronize()
-            ref = getattr(np, f)(x.astype(np.float64))
+            xd = x.astype(np.float64)
+            ref = getattr(np, f)(xd)
             err = np.abs(y.cpu().numpy() - ref)
             if f == "tan":
-                err = err / np.maximum(1.0, np.abs(ref))
+                # the __tanf intrinsic loses accuracy next to the poles
+                keep = np.abs(np.cos(xd)) > 1e-2
+                err = err[keep] / np.maximum(1.0, np.abs(ref[keep]))
             assert err.max() < (1e-5 if not fast else 2e-2)
 
 
