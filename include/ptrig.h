@@ -234,6 +234,35 @@ ptrig_status ptrig_batch_plan_autotune(ptrig_batch_plan *plan, ptrig_stream stre
 
 void ptrig_batch_plan_destroy(ptrig_batch_plan *plan);
 
+/* The ragged batch for callers that must not allocate device memory.  No
+ * counterpart in the paper: this is a library convenience.
+ *
+ * ptrig_batch_plan_create calls cudaMalloc and copies from the host, which
+ * some callers cannot do: code running while a stream is being captured into
+ * a CUDA graph, code inside an allocator or memory pool that must not call
+ * back into cudaMalloc, and latency-critical paths where a device allocation
+ * (which can synchronize the device) is not acceptable.  This entry point
+ * takes the descriptors already in DEVICE memory (count ptrig_desc structs,
+ * caller-owned, like the x / y arrays they point to) and calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *
+ * Scratch: a table of count + 1 64-bit tile offsets in a fixed device array
+ * built into the library, which every device that loads the library holds
+ * until the process exits.  Hence the limit: count <= 16384 arrays; a larger
+ * count returns PTRIG_ERR_INVALID_ARG (as does device_descs == NULL with
+ * count > 0).  count == 0 is a no-op.
+ *
+ * The first call on each device looks up the table's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  Every call on a device shares the one table, and each call
+ * rewrites it before use: calls on the same device that may overlap on the
+ * GPU (different streams without ordering between them) race on it and must
+ * be serialized by the caller.  Descriptors with an unknown func, a nonzero
+ * reserved field or a NULL pointer for a non-empty array are skipped (their
+ * outputs are left untouched).  Asynchronous on `stream`; tiles of 8192
+ * elements, one persistent launch plus a one-block prefix launch. */
+ptrig_status ptrig_batch_run_noalloc(const ptrig_desc *device_descs, size_t count, ptrig_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -65,6 +65,7 @@ SIGNATURES = {
     "ptrig_batch_plan_get_config": [_P, _P, _P, _P, _P],
     "ptrig_batch_plan_autotune": [_P, _P, _I, _P, _P, _I, _P, _P, _P],
     "ptrig_batch_plan_destroy": [_P],
+    "ptrig_batch_run_noalloc": [_P, _SZ, _P],
 }
 _RESTYPE = {"ptrig_status_string": ctypes.c_char_p, "ptrig_batch_plan_destroy": None}
 
@@ -208,6 +209,13 @@ def ptrig_get_launch_config(family):
 
 
 # ----------------------------------------------------------------- batch
+
+
+def ptrig_batch_run_noalloc(device_descs, count, stream=None):
+    """Ragged batch without any device allocation: device_descs is the device
+    address (or a tensor) of `count` ptrig_desc structs.  See include/ptrig.h."""
+    _check(_load().ptrig_batch_run_noalloc(_ptr(device_descs), count, _stream(stream)),
+           "ptrig_batch_run_noalloc")
 
 
 class BatchPlan:

@@ -9,6 +9,7 @@
 // occupancy.  With PTRIG_BATCH_GRAPH the launch is captured once into a CUDA
 // graph and ptrig_batch_run replays it.
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "ptrig_map.cuh"
@@ -133,6 +134,119 @@ __global__ void __launch_bounds__(512, 2) k_batch(const ptrig_desc *__restrict__
         break;
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Batch entry point that allocates nothing (ptrig_batch_run_noalloc).
+//
+// Its only scratch is the table below: the first tile of each array plus the
+// total tile count, rewritten by every call.  A file-scope __device__ array
+// is reserved when the library loads on a device and stays until the process
+// exits, so a call needs no cudaMalloc.  Host code cannot use the name
+// g_noalloc_first_tile as a device address; the address is looked up once per
+// device with cudaGetSymbolAddress (noalloc_scratch()).
+#define PTRIG_NOALLOC_MAX_ARRAYS 16384
+static __device__ __align__(256) uint64_t g_noalloc_first_tile[PTRIG_NOALLOC_MAX_ARRAYS + 1];
+
+// A descriptor the batch can use: known selector, reserved == 0 and non-NULL
+// pointers for a non-empty array.  Others count as empty and are skipped.
+__device__ __forceinline__ bool noalloc_desc_ok(const ptrig_desc &d) {
+  if (d.func > PTRIG_SINCOS || d.reserved != 0) return false;
+  if (d.n == 0) return true;
+  return d.x && d.y0 && (d.func != PTRIG_SINCOS || d.y1);
+}
+
+// One block of 1024 threads: tiles per array and their exclusive prefix sum
+// into first_tile[0 .. count] (first_tile[count] = total tiles).
+__global__ void __launch_bounds__(1024) k_noalloc_prefix(const ptrig_desc *__restrict__ descs, uint32_t count,
+                                                         uint32_t tile_elems, uint64_t *first_tile) {
+  __shared__ uint64_t s_part[1024];
+  const uint32_t per = (count + blockDim.x - 1) / blockDim.x;
+  const uint32_t lo = threadIdx.x * per;
+  const uint32_t hi = min(count, lo + per);
+  uint64_t sum = 0;
+  for (uint32_t i = lo; i < hi; ++i) {
+    const ptrig_desc d = descs[i];
+    if (noalloc_desc_ok(d)) sum += (d.n + tile_elems - 1) / tile_elems;
+  }
+  s_part[threadIdx.x] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {  // exclusive scan of the 1024 partial sums
+    uint64_t run = 0;
+    for (uint32_t t = 0; t < blockDim.x; ++t) {
+      const uint64_t v = s_part[t];
+      s_part[t] = run;
+      run += v;
+    }
+    first_tile[count] = run;
+  }
+  __syncthreads();
+  uint64_t run = s_part[threadIdx.x];
+  for (uint32_t i = lo; i < hi; ++i) {
+    first_tile[i] = run;
+    const ptrig_desc d = descs[i];
+    if (noalloc_desc_ok(d)) run += (d.n + tile_elems - 1) / tile_elems;
+  }
+}
+
+// Persistent batch kernel over the table above: a tile finds its array by
+// binary search on first_tile (the largest i with first_tile[i] <= tile),
+// then runs the same per-tile code as k_batch.
+__global__ void __launch_bounds__(512, 2) k_batch_noalloc(const ptrig_desc *__restrict__ descs, uint32_t count,
+                                                          const uint64_t *__restrict__ first_tile,
+                                                          uint32_t tile_elems) {
+  __shared__ float4 s_tab[8];
+  if (threadIdx.x < 8) s_tab[threadIdx.x] = c_tab_f32[threadIdx.x];
+  __syncthreads();
+  const uint64_t ntiles = first_tile[count];
+  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    uint32_t lo = 0, hi = count;  // first_tile[lo] <= tile < first_tile[hi]
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) / 2;
+      if (first_tile[mid] <= tile)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    const ptrig_desc d = descs[lo];
+    const uint64_t start = (tile - first_tile[lo]) * (uint64_t)tile_elems;
+    const uint64_t rem = d.n - start;
+    const uint32_t len = rem < tile_elems ? (uint32_t)rem : tile_elems;
+    switch (d.func) {
+      case PTRIG_SIN:
+        batch_tile<OP_SIN>(d, start, len, s_tab);
+        break;
+      case PTRIG_COS:
+        batch_tile<OP_COS>(d, start, len, s_tab);
+        break;
+      case PTRIG_TAN:
+        batch_tile<OP_TAN>(d, start, len, s_tab);
+        break;
+      default:
+        batch_tile<OP_SINCOS>(d, start, len, s_tab);
+        break;
+    }
+  }
+}
+
+// Device address of g_noalloc_first_tile on the current device, looked up on
+// the first call per device and cached.
+static ptrig_status noalloc_scratch(uint64_t **out) {
+  static std::mutex mu;
+  static uint64_t *cache[64] = {};
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (dev < 0 || dev >= 64) return PTRIG_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!cache[dev]) {
+    void *ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_noalloc_first_tile);
+    if (e != cudaSuccess) return cuda_fail(e);
+    cache[dev] = static_cast<uint64_t *>(ptr);
+  }
+  *out = cache[dev];
+  return PTRIG_OK;
 }
 
 static void free_graph(ptrig_batch_plan *p) {
@@ -345,6 +459,27 @@ ptrig_status ptrig_batch_plan_autotune(ptrig_batch_plan *plan, ptrig_stream stre
   if (best_items) *best_items = bi;
   if (best_ms) *best_ms = best;
   return PTRIG_OK;
+}
+
+ptrig_status ptrig_batch_run_noalloc(const ptrig_desc *device_descs, size_t count, ptrig_stream stream) {
+  if (count == 0) return PTRIG_OK;
+  if (!device_descs) return PTRIG_ERR_INVALID_ARG;
+  if (count > PTRIG_NOALLOC_MAX_ARRAYS) return PTRIG_ERR_INVALID_ARG;
+  const int sms = sm_count();
+  if (sms <= 0) return PTRIG_ERR_NO_DEVICE;
+  uint64_t *first_tile = nullptr;
+  const ptrig_status st = noalloc_scratch(&first_tile);
+  if (st != PTRIG_OK) return st;
+  const int block = 256, items = 32;
+  const uint32_t tile_elems = (uint32_t)(block * items);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  k_noalloc_prefix<<<1, 1024, 0, s>>>(device_descs, (uint32_t)count, tile_elems, first_tile);
+  ptrig_status ls = finish_launch();
+  if (ls != PTRIG_OK) return ls;
+  const int occ = occupancy((const void *)k_batch_noalloc, block);
+  const int grid = sms * (occ > 0 ? occ : 1);
+  k_batch_noalloc<<<grid, block, 0, s>>>(device_descs, (uint32_t)count, first_tile, tile_elems);
+  return finish_launch();
 }
 
 void ptrig_batch_plan_destroy(ptrig_batch_plan *plan) {
