@@ -38,9 +38,6 @@ METRIC = "Gelem/s & % HBM peak, π/12 sin/cos/tan on 2^28 fp32; packed-half vs p
 WORKLOAD = ("bandwidth: 2^28 fp32 angles, 80% U[-100pi,100pi], 10% within 1e-4 of k*pi/12, "
             "10% within 1e-3 of odd multiples of pi/2; step = proposed sin, cos, tan, sincos + "
             "Taylor-5 sin, cos, tan (one launch each)")
-# (name, bytes moved per element)
-STEP_KERNELS = [("sin_f32", 8), ("cos_f32", 8), ("tan_f32", 8), ("sincos_f32", 12),
-                ("taylor_sin_f32", 8), ("taylor_cos_f32", 8), ("taylor_tan_f32", 8)]
 
 
 def _peaks():
@@ -178,12 +175,126 @@ def run_reference(args, rank, world):
 # --------------------------------------------------------------------- GPU
 
 
+class Kernel:
+    """One kernel launch of a step: name, algorithmic bytes per launch,
+    angles evaluated per launch, and the call that launches it."""
+
+    def __init__(self, name, nbytes, elems, call, launches=1):
+        self.name, self.nbytes, self.elems, self.call, self.launches = name, nbytes, elems, call, launches
+
+
+def workload_bandwidth(B, W, torch, dev, rank, log2n):
+    n = 1 << log2n
+    x_host = W.bandwidth(n, seed=W.SEED + rank)
+    x = torch.from_numpy(x_host).to(dev)
+    o = [torch.empty_like(x) for _ in range(2)]
+    s = torch.cuda.current_stream().cuda_stream
+    ks = [Kernel("sin_f32", 8 * n, n, lambda: B.ptrig_sin_f32(x, o[0], n, s)),
+          Kernel("cos_f32", 8 * n, n, lambda: B.ptrig_cos_f32(x, o[0], n, s)),
+          Kernel("tan_f32", 8 * n, n, lambda: B.ptrig_tan_f32(x, o[0], n, s)),
+          Kernel("sincos_f32", 12 * n, n, lambda: B.ptrig_sincos_f32(x, o[0], o[1], n, s)),
+          Kernel("taylor_sin_f32", 8 * n, n, lambda: B.ptrig_taylor_sin_f32(x, o[0], n, s)),
+          Kernel("taylor_cos_f32", 8 * n, n, lambda: B.ptrig_taylor_cos_f32(x, o[0], n, s)),
+          Kernel("taylor_tan_f32", 8 * n, n, lambda: B.ptrig_taylor_tan_f32(x, o[0], n, s))]
+    meta = {"metric": METRIC, "dtype": "f32", "workload": WORKLOAD, "n_per_gpu": n,
+            "l2": "inputs larger than L2 (1 GiB vs 129 MB), no flush"}
+    return ks, meta, {"x": x, "x_host": x_host, "n": n}
+
+
+def workload_half(B, W, torch, dev, rank, log2n):
+    import numpy as np
+    n = 1 << log2n
+    xs = {"f16": torch.from_numpy(W.half16(n, seed=W.SEED + rank).view(np.int16)).to(dev),
+          "bf16": torch.from_numpy(W.half_bf16(n, seed=W.SEED + rank).view(np.int16)).to(dev)}
+    o = [torch.empty_like(xs["f16"]) for _ in range(2)]
+    s = torch.cuda.current_stream().cuda_stream
+    ks = []
+    for dt, x in xs.items():
+        for f in ("sin", "cos", "tan"):
+            ks.append(Kernel(f"{f}_{dt}", 4 * n, n, (lambda f=f, dt=dt, x=x: getattr(B, f"ptrig_{f}_{dt}")(x, o[0], n, s))))
+        ks.append(Kernel(f"sincos_{dt}", 6 * n, n, (lambda dt=dt, x=x: getattr(B, f"ptrig_sincos_{dt}")(x, o[0], o[1], n, s))))
+    meta = {"metric": "Gelem/s, pi/12 sin/cos/tan/sincos on 2^28 angles stored as fp16 and bf16 (FP32 math)",
+            "dtype": "f16/bf16 storage, f32 math",
+            "workload": "precision: bandwidth mixture as fp16 (uniform part |x| <= 60) and as bf16, 2^28 each; "
+                        "step = sin, cos, tan, sincos for both types", "n_per_gpu": n,
+            "l2": "inputs larger than L2 (512 MiB vs 129 MB), no flush"}
+    return ks, meta, {}
+
+
+def workload_large(B, W, torch, dev, rank, log2n):
+    n = 1 << min(log2n, 24)
+    x = torch.from_numpy(W.large(n, seed=W.SEED + rank)).to(dev)
+    o = [torch.empty_like(x) for _ in range(2)]
+    s = torch.cuda.current_stream().cuda_stream
+    ks = [Kernel("sin_f32", 8 * n, n, lambda: B.ptrig_sin_f32(x, o[0], n, s)),
+          Kernel("cos_f32", 8 * n, n, lambda: B.ptrig_cos_f32(x, o[0], n, s)),
+          Kernel("tan_f32", 8 * n, n, lambda: B.ptrig_tan_f32(x, o[0], n, s)),
+          Kernel("sincos_f32", 12 * n, n, lambda: B.ptrig_sincos_f32(x, o[0], o[1], n, s))]
+    meta = {"metric": "Gelem/s, pi/12 sin/cos/tan/sincos on 2^24 fp32 angles with |x| log-uniform in [1, 1e5]",
+            "dtype": "f32 (FP64 reduction above 2^10 pi)",
+            "workload": "precision: 2^24 fp32, |x| log-uniform in [1, 1e5], random sign (about 30% take the FP64 "
+                        "Cody-Waite side path)", "n_per_gpu": n,
+            "l2": "64 MiB input, smaller than L2: compute-bound (FP64 side path), no flush"}
+    return ks, meta, {}
+
+
+def workload_batch(B, W, torch, dev, rank, log2n):
+    lengths, sel = W.batch_spec(4096, seed=W.SEED + rank)
+    total = int(lengths.sum())
+    xs = torch.empty(total, dtype=torch.float32, device=dev)
+    y0 = torch.empty_like(xs)
+    y1 = torch.empty_like(xs)
+    descs, off, nbytes = [], 0, 0
+    # arrays start on 16-byte boundaries inside one allocation
+    for i, (n, f) in enumerate(zip(lengths, sel)):
+        n = int(n)
+        xs[off:off + n] = torch.from_numpy(W.batch_array(i, n, seed=W.SEED + rank)).to(dev)
+        descs.append((xs[off:off + n], y0[off:off + n], y1[off:off + n] if f == 3 else None, n, int(f)))
+        nbytes += (12 if f == 3 else 8) * n
+        off += n
+    plan = B.BatchPlan(descs, B.BATCH_GRAPH)
+    tuned = plan.autotune(reps=3)
+    s = torch.cuda.current_stream().cuda_stream
+    ks = [Kernel("batch_graph", nbytes, total, lambda: plan.run(s))]
+    meta = {"metric": "Gelem/s, ragged batch of 4096 fp32 arrays (per-array sin/cos/tan/sincos) in one persistent "
+                      "launch captured in a CUDA graph",
+            "dtype": "f32", "workload": f"batching: 4096 arrays, lengths floor(exp U[ln 100, ln 1e6]) "
+                                        f"(total {total}), values U[-8pi, 8pi], selectors uniform",
+            "n_per_gpu": total, "l2": "inputs larger than L2, no flush", "autotuned": tuned}
+    return ks, meta, {"plan": plan, "descs": descs}
+
+
+def workload_autograd(B, W, torch, dev, rank, log2n):
+    from paper_2502_10831_gb300 import functional as Fn
+    x_h, w_h, v_h, u_h = W.autograd((8192, 4096), seed=W.SEED + rank)
+    x = torch.from_numpy(x_h).to(dev).requires_grad_(True)
+    w, v, u = (torch.from_numpy(a).to(dev) for a in (w_h, v_h, u_h))
+    n = x.numel()
+
+    def fwd_bwd():
+        x.grad = None
+        loss = (w * Fn.sin(x) + v * Fn.cos(x) + u * torch.clamp(Fn.tan(x), -50, 50)).sum()
+        loss.backward()
+
+    ks = [Kernel("loss_fwd_bwd", 4 * n * 10, n, fwd_bwd, launches=6)]
+    meta = {"metric": "Gelem/s, forward + backward of sum(w sin + v cos + u clamp(tan, -50, 50)) over [8192, 4096] "
+                      "fp32 (autograd.Function, hand-written derivative kernels)",
+            "dtype": "f32", "workload": "differentiation: x U[-4pi, 4pi], w, v, u ~ N(0,1), [8192, 4096]",
+            "n_per_gpu": n, "l2": "inputs larger than L2, no flush"}
+    return ks, meta, {}
+
+
+WORKLOADS = {"bandwidth": workload_bandwidth, "half": workload_half, "large": workload_large,
+             "batch": workload_batch, "autograd": workload_autograd}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ptrig", choices=["ptrig", "reference"])
+    ap.add_argument("--workload", default="bandwidth", choices=sorted(WORKLOADS))
     ap.add_argument("--log2n", type=int, default=28)
     ap.add_argument("--no-extras", action="store_true", help="skip half/cuda-math/e2e/cpu legs")
     args = ap.parse_args()
@@ -196,7 +307,6 @@ def main():
     if args.impl == "reference":
         return run_reference(args, rank, world)
 
-    import numpy as np
     import torch
 
     from paper_2502_10831_gb300 import binding as B
@@ -210,34 +320,20 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     Bld.build()
     B.lib()
-    n = 1 << args.log2n
-    x_host = W.bandwidth(n, seed=W.SEED + rank)
     dev = torch.device("cuda", local)
-    x = torch.from_numpy(x_host).to(dev)
-    outs = [torch.empty_like(x) for _ in range(2)]
+    kernels_list, meta, state = WORKLOADS[args.workload](B, W, torch, dev, rank, args.log2n)
     stream = torch.cuda.current_stream()
-    s_ptr = stream.cuda_stream
-
-    calls = {
-        "sin_f32": lambda: B.ptrig_sin_f32(x, outs[0], n, s_ptr),
-        "cos_f32": lambda: B.ptrig_cos_f32(x, outs[0], n, s_ptr),
-        "tan_f32": lambda: B.ptrig_tan_f32(x, outs[0], n, s_ptr),
-        "sincos_f32": lambda: B.ptrig_sincos_f32(x, outs[0], outs[1], n, s_ptr),
-        "taylor_sin_f32": lambda: B.ptrig_taylor_sin_f32(x, outs[0], n, s_ptr),
-        "taylor_cos_f32": lambda: B.ptrig_taylor_cos_f32(x, outs[0], n, s_ptr),
-        "taylor_tan_f32": lambda: B.ptrig_taylor_tan_f32(x, outs[0], n, s_ptr),
-    }
 
     def step():
-        for name, _ in STEP_KERNELS:
-            calls[name]()
+        for k in kernels_list:
+            k.call()
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
 
     # timed region: K steps, events around every kernel on the launching stream
-    nk = len(STEP_KERNELS)
+    nk = len(kernels_list)
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(nk + 1)] for _ in range(args.steps)]
     clocks = ClockSampler(local)
     clocks.start()
@@ -251,8 +347,8 @@ def main():
     t0.record(stream)
     for s in range(args.steps):
         ev[s][0].record(stream)
-        for k, (name, _) in enumerate(STEP_KERNELS):
-            calls[name]()
+        for k, kern in enumerate(kernels_list):
+            kern.call()
             ev[s][k + 1].record(stream)
     t1.record(stream)
     torch.cuda.synchronize()
@@ -268,37 +364,47 @@ def main():
     per_kernel_ms = [statistics.mean(ev[s][k].elapsed_time(ev[s][k + 1]) for s in range(args.steps))
                      for k in range(nk)]
     ms_per_step = total_ms / args.steps
-    evals = nk * n * world
+    evals = sum(k.elems for k in kernels_list) * world
     value = evals / (ms_per_step * 1e-3) / 1e9
     peak, peak_kind = _peaks()
     kernels = {}
-    for (name, bpe), ms in zip(STEP_KERNELS, per_kernel_ms):
-        gbs = bpe * n / (ms * 1e-3) / 1e9
-        kernels[name] = {"ms": round(ms, 4), "gelem_s": round(n / (ms * 1e-3) / 1e9, 2),
-                         "gb_s": round(gbs, 1), "hbm_frac": round(gbs / peak, 4)}
+    for kern, ms in zip(kernels_list, per_kernel_ms):
+        gbs = kern.nbytes / (ms * 1e-3) / 1e9
+        kernels[kern.name] = {"ms": round(ms, 4), "gelem_s": round(kern.elems / (ms * 1e-3) / 1e9, 2),
+                              "gb_s": round(gbs, 1), "hbm_frac": round(gbs / peak, 4)}
     dom_i = max(range(nk), key=lambda k: per_kernel_ms[k])
-    dom_name, dom_bpe = STEP_KERNELS[dom_i]
-    achieved = dom_bpe * n / (per_kernel_ms[dom_i] * 1e-3) / 1e9
+    dom = kernels_list[dom_i]
+    achieved = dom.nbytes / (per_kernel_ms[dom_i] * 1e-3) / 1e9
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tpath):
-        traffic = json.load(open(tpath)).get(dom_name)
-    roofline = {"bound": "hbm", "kernel": dom_name, "achieved": round(achieved, 1), "peak": peak,
-                "peak_kind": f"{peak_kind} (MEASURED_PEAKS hbm_gbs copy)" if peak_kind == "measured" else peak_kind,
+        tr = json.load(open(tpath)).get(dom.name)
+        traffic = tr.get("bytes_per_launch") if isinstance(tr, dict) else tr
+    roofline = {"bound": "hbm", "kernel": dom.name, "achieved": round(achieved, 1), "peak": peak,
+                "peak_kind": "measured (MEASURED_PEAKS.json hbm_gbs, copy)" if peak_kind == "measured" else peak_kind,
                 "unit": "GB/s", "frac": round(achieved / peak, 4),
-                "algorithmic_bytes_per_launch": dom_bpe * n, "traffic": traffic}
-
-    line = {"metric": METRIC, "value": round(value, 2), "unit": "Gelem/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_per_gpu": n, "l2": "inputs larger than L2 (1 GiB vs 129 MB), no flush",
-                       "launch_config_f32": B.ptrig_get_launch_config(B.FAMILY_F32),
-                       "launch_config_taylor": B.ptrig_get_launch_config(B.FAMILY_TAYLOR)},
-            "roofline": roofline, "kernels": kernels, "gpu_launches": nk * args.steps, "clocks": clk,
+                "algorithmic_bytes_per_launch": dom.nbytes, "traffic": traffic}
+    config = {"workload": meta["workload"], "n_per_gpu": meta["n_per_gpu"], "l2": meta["l2"],
+              "launch_config_f32": B.ptrig_get_launch_config(B.FAMILY_F32),
+              "launch_config_half": B.ptrig_get_launch_config(B.FAMILY_HALF),
+              "launch_config_taylor": B.ptrig_get_launch_config(B.FAMILY_TAYLOR)}
+    if "autotuned" in meta:
+        config["batch_autotuned"] = meta["autotuned"]
+    line = {"metric": meta["metric"], "value": round(value, 2), "unit": "Gelem/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": meta["dtype"],
+            "data": "synthetic", "config": config, "roofline": roofline, "kernels": kernels,
+            "gpu_launches": sum(k.launches for k in kernels_list) * args.steps, "clocks": clk,
             "wall_s_timed": round(wall, 3)}
-
-    if not args.no_extras and rank == 0:
-        line.update(extras(args, B, W, x, x_host, n, stream, peak, kernels))
+    if args.workload != "bandwidth":
+        line["workload"] = args.workload
+    if args.workload == "batch" and rank == 0:
+        plan = state["plan"]
+        ms = _time_call(lambda: plan.run_per_array(stream.cuda_stream), 3, stream)
+        line["per_array_launches"] = {"ms": round(ms, 3), "gelem_s": round(meta["n_per_gpu"] / ms / 1e6, 2),
+                                      "launches": len(state["descs"])}
+    if args.workload == "bandwidth" and not args.no_extras and rank == 0:
+        line.update(extras(args, B, W, state["x"], state["x_host"], state["n"], stream, peak, kernels))
     if rank == 0:
         print(json.dumps(line))
     if dist:

@@ -66,11 +66,11 @@ int occupancy(const void *kernel, int block) {
   return nb;
 }
 
-// Defaults measured on GB300 (2^28 angles): FP32 families 128 threads with
-// four 16-byte loads in flight, one-shot chunks; fp16 / bf16 512 threads, one
-// load in flight, persistent grid of 8 blocks per SM.
+// Defaults measured on GB300 (2^28 angles): every family runs 128 threads with
+// four 16-byte loads in flight per thread, one-shot chunks (one contiguous
+// 8 KiB block of input per block).
 static std::mutex g_cfg_mu;
-static LaunchCfg g_cfg[PTRIG_FAMILY_COUNT] = {{128, 4, 0}, {512, 1, 8}, {128, 4, 0}, {128, 4, 0}};
+static LaunchCfg g_cfg[PTRIG_FAMILY_COUNT] = {{128, 4, 0}, {128, 4, 0}, {128, 4, 0}, {128, 4, 0}};
 
 LaunchCfg get_cfg(int family) {
   std::lock_guard<std::mutex> lk(g_cfg_mu);

@@ -238,11 +238,17 @@ __device__ __forceinline__ uint32_t table_index(float t, uint32_t jb) {
   return ((jb & 1u) << 2) | ((uint32_t)kq & 3u);
 }
 
-// Two angles of the fast range at once: packed FP32 for the reduction, the
-// segment scaling, h^2 and the final products; table lookup, MUFU and signs
-// per lane.  Bit-identical to two calls of Proposed<OP>::eval<false>.
+// Pair form for 16-bit storage: magnitudes m0 (and m1 for sincos), all >= 0,
+// and one sign word per output whose bits 15 and 31 are the signs of lanes 0
+// and 1 -- the sign positions of a packed half2 / bfloat162 word, so that one
+// XOR signs both lanes after rounding (round-to-nearest is sign-symmetric, so
+// this equals rounding the signed value).  The lanes' j and r sign bits are
+// gathered into one word with byte permutes before the sign_bits() logic:
+//   J = {.., jb0.byte0, .., jb1.byte0}: p at bits 8 / 24, j1 at bits 9 / 25
+//   R = {.., r0.byte3, .., r1.byte3}:   sr at bits 15 / 31
 template <int OP>
-__device__ __forceinline__ void proposed_pair(float2 x, const float4 *tab, float2 &o0, float2 &o1) {
+__device__ __forceinline__ void proposed_pair_mag(float2 x, const float4 *tab, float2 &m0, float2 &m1,
+                                                  uint32_t &s0, uint32_t &s1) {
   const RedF2 red = reduce_fast2(x);
   const float2 t = make_float2(fabsf(red.r.x), fabsf(red.r.y));
   const float2 v = __fmul2_rn(t, make_float2(PTRIG_12_OVER_PI_F, PTRIG_12_OVER_PI_F));
@@ -252,25 +258,27 @@ __device__ __forceinline__ void proposed_pair(float2 x, const float4 *tab, float
   const float4 c1 = tab[i1];
   const float2 N = make_float2(__fmaf_rn(c0.x, t.x, c0.y), __fmaf_rn(c1.x, t.y, c1.y));
   const float2 D = make_float2(__fmaf_rn(c0.z, t.x, c0.w), __fmaf_rn(c1.z, t.y, c1.w));
-  const Signs g0 = sign_bits(red.jb0, __float_as_uint(red.r.x));
-  const Signs g1 = sign_bits(red.jb1, __float_as_uint(red.r.y));
+  const uint32_t J = __byte_perm(red.jb0, red.jb1, 0x4000);
+  const uint32_t R = __byte_perm(__float_as_uint(red.r.x), __float_as_uint(red.r.y), 0x7030);
+  const uint32_t A = J << 6;  // j1 at bits 15 / 31
+  const uint32_t P = J << 7;  // p at bits 15 / 31
   if (OP == OP_TAN) {
-    const float2 q = __fmul2_rn(N, make_float2(rcp_approx(D.x), rcp_approx(D.y)));
-    o0 = make_float2(xor_sign(q.x, g0.t), xor_sign(q.y, g1.t));
+    m0 = __fmul2_rn(N, make_float2(rcp_approx(D.x), rcp_approx(D.y)));
+    s0 = P ^ R;
   } else {
     const float2 h2 = __ffma2_rn(N, N, __fmul2_rn(D, D));
     const float2 rs = make_float2(rsqrt_approx(h2.x), rsqrt_approx(h2.y));
     if (OP == OP_SIN || OP == OP_SINCOS) {
-      const float2 sv = __fmul2_rn(N, rs);
-      o0 = make_float2(xor_sign(sv.x, g0.s), xor_sign(sv.y, g1.s));
+      m0 = __fmul2_rn(N, rs);
+      s0 = A ^ (R & ~P);
     }
-    if (OP == OP_COS || OP == OP_SINCOS) {
-      const float2 cv = __fmul2_rn(D, rs);
-      const float2 c = make_float2(xor_sign(cv.x, g0.c), xor_sign(cv.y, g1.c));
-      if (OP == OP_COS)
-        o0 = c;
-      else
-        o1 = c;
+    if (OP == OP_COS) {
+      m0 = __fmul2_rn(D, rs);
+      s0 = A ^ (P & ~R);
+    }
+    if (OP == OP_SINCOS) {
+      m1 = __fmul2_rn(D, rs);
+      s1 = A ^ (P & ~R);
     }
   }
 }
@@ -289,8 +297,9 @@ struct Proposed {
   static constexpr int NOUT = (OP == OP_SINCOS) ? 2 : 1;
   static constexpr bool HAS_SLOW = true;
   static constexpr bool HAS_PAIR = true;
-  __device__ __forceinline__ static void eval_pair(float2 x, const float4 *tab, float2 &o0, float2 &o1) {
-    proposed_pair<OP>(x, tab, o0, o1);
+  __device__ __forceinline__ static void eval_pair_mag(float2 x, const float4 *tab, float2 &m0, float2 &m1,
+                                                       uint32_t &s0, uint32_t &s1) {
+    proposed_pair_mag<OP>(x, tab, m0, m1, s0, s1);
   }
   template <bool FULL = true>
   __device__ __forceinline__ static void eval(float x, const float4 *tab, float &o0, float &o1) {
@@ -331,7 +340,8 @@ struct Taylor {
   static constexpr int NOUT = 1;
   static constexpr bool HAS_SLOW = true;
   static constexpr bool HAS_PAIR = false;
-  __device__ __forceinline__ static void eval_pair(float2, const float4 *, float2 &, float2 &) {}
+  __device__ __forceinline__ static void eval_pair_mag(float2, const float4 *, float2 &, float2 &, uint32_t &,
+                                                       uint32_t &) {}
   template <bool FULL = true>
   __device__ __forceinline__ static void eval(float x, const float4 *, float &o0, float &) {
     const RedF red = reduce_sel<FULL>(x);
@@ -454,6 +464,15 @@ struct Storage<float> {
 template <>
 struct Storage<__half> {
   static constexpr int EPV = 8;
+  __device__ __forceinline__ static float2 to_float2(uint32_t w) {
+    __half2 h;
+    *reinterpret_cast<uint32_t *>(&h) = w;
+    return __half22float2(h);
+  }
+  __device__ __forceinline__ static uint32_t from_float2(float2 v) {
+    const __half2 h = __float22half2_rn(v);
+    return *reinterpret_cast<const uint32_t *>(&h);
+  }
   __device__ __forceinline__ static void unpack(const uint4 &v, float (&f)[8]) {
     const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
@@ -481,6 +500,13 @@ struct Storage<__half> {
 template <>
 struct Storage<__nv_bfloat16> {
   static constexpr int EPV = 8;
+  __device__ __forceinline__ static float2 to_float2(uint32_t w) {
+    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+  }
+  __device__ __forceinline__ static uint32_t from_float2(float2 v) {
+    const __nv_bfloat162 h = __float22bfloat162_rn(v);
+    return *reinterpret_cast<const uint32_t *>(&h);
+  }
   __device__ __forceinline__ static void unpack(const uint4 &v, float (&f)[8]) {
     const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll

@@ -54,7 +54,8 @@ struct CudaMath {
   static constexpr int NOUT = (OP == OP_SINCOS) ? 2 : 1;
   static constexpr bool HAS_SLOW = false;
   static constexpr bool HAS_PAIR = false;
-  __device__ __forceinline__ static void eval_pair(float2, const float4 *, float2 &, float2 &) {}
+  __device__ __forceinline__ static void eval_pair_mag(float2, const float4 *, float2 &, float2 &, uint32_t &,
+                                                       uint32_t &) {}
   template <bool FULL = true>
   __device__ __forceinline__ static void eval(float x, const float4 *, float &o0, float &o1) {
     if (FAST) {

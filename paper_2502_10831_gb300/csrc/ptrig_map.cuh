@@ -18,8 +18,39 @@ namespace ptrig {
 // false, storing nothing, when an element lies outside the FP32 reduction
 // range (or is NaN / inf); the caller then hands the rest of its work to the
 // full-reduction path.
+// 16-bit storage with the pair form: lanes stay in float2 from the packed
+// input word to the packed output word; signs are applied to the rounded
+// word with one XOR per output word.
+template <typename T, class F>
+__device__ __forceinline__ bool map_vector_fast_h(uint4 v, size_t i, T *y0, T *y1, const float4 *tab) {
+  using S = Storage<T>;
+  const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+  float2 f[4];
+  bool slow = false;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    f[k] = S::to_float2(w[k]);
+    slow |= needs_slow(f[k].x);
+    slow |= needs_slow(f[k].y);
+  }
+  if (slow) return false;
+  uint32_t a[4], b[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    float2 m0, m1;
+    uint32_t s0, s1;
+    F::eval_pair_mag(f[k], tab, m0, m1, s0, s1);
+    a[k] = S::from_float2(m0) ^ (s0 & 0x80008000u);
+    if constexpr (F::NOUT == 2) b[k] = S::from_float2(m1) ^ (s1 & 0x80008000u);
+  }
+  st_stream(reinterpret_cast<uint4 *>(y0) + i, make_uint4(a[0], a[1], a[2], a[3]));
+  if constexpr (F::NOUT == 2) st_stream(reinterpret_cast<uint4 *>(y1) + i, make_uint4(b[0], b[1], b[2], b[3]));
+  return true;
+}
+
 template <typename T, class F>
 __device__ __forceinline__ bool map_vector_fast(uint4 v, size_t i, T *y0, T *y1, const float4 *tab) {
+  if constexpr (F::HAS_PAIR && sizeof(T) == 2) return map_vector_fast_h<T, F>(v, i, y0, y1, tab);
   using S = Storage<T>;
   constexpr int E = S::EPV;
   float f[E], o0[E], o1[E];
@@ -30,23 +61,8 @@ __device__ __forceinline__ bool map_vector_fast(uint4 v, size_t i, T *y0, T *y1,
     for (int e = 0; e < E; ++e) slow |= needs_slow(f[e]);
     if (slow) return false;
   }
-  // packed FP32 pairs where the kernel is instruction-bound (16-bit storage:
-  // half the bytes per angle); FP32 storage is memory-bound and keeps the
-  // scalar form, which needs fewer registers
-  if constexpr (F::HAS_PAIR && sizeof(T) == 2) {
 #pragma unroll
-    for (int e = 0; e < E; e += 2) {
-      float2 a, b;
-      F::eval_pair(make_float2(f[e], f[e + 1]), tab, a, b);
-      o0[e] = a.x;
-      o0[e + 1] = a.y;
-      o1[e] = b.x;
-      o1[e + 1] = b.y;
-    }
-  } else {
-#pragma unroll
-    for (int e = 0; e < E; ++e) F::template eval<false>(f[e], tab, o0[e], o1[e]);
-  }
+  for (int e = 0; e < E; ++e) F::template eval<false>(f[e], tab, o0[e], o1[e]);
   st_stream(reinterpret_cast<uint4 *>(y0) + i, S::pack(o0));
   if constexpr (F::NOUT == 2) st_stream(reinterpret_cast<uint4 *>(y1) + i, S::pack(o1));
   return true;
