@@ -241,17 +241,17 @@ def workload_large(B, W, torch, dev, rank, log2n):
 def workload_batch(B, W, torch, dev, rank, log2n):
     lengths, sel = W.batch_spec(4096, seed=W.SEED + rank)
     total = int(lengths.sum())
-    xs = torch.empty(total, dtype=torch.float32, device=dev)
+    padded = int(sum((int(n) + 63) // 64 * 64 for n in lengths))
+    xs = torch.empty(padded, dtype=torch.float32, device=dev)
     y0 = torch.empty_like(xs)
     y1 = torch.empty_like(xs)
     descs, off, nbytes = [], 0, 0
-    # arrays start on 16-byte boundaries inside one allocation
     for i, (n, f) in enumerate(zip(lengths, sel)):
         n = int(n)
         xs[off:off + n] = torch.from_numpy(W.batch_array(i, n, seed=W.SEED + rank)).to(dev)
         descs.append((xs[off:off + n], y0[off:off + n], y1[off:off + n] if f == 3 else None, n, int(f)))
         nbytes += (12 if f == 3 else 8) * n
-        off += n
+        off += (n + 63) // 64 * 64  # each array starts on a 256-byte boundary, as separate allocations would
     plan = B.BatchPlan(descs, B.BATCH_GRAPH)
     tuned = plan.autotune(reps=3)
     s = torch.cuda.current_stream().cuda_stream
@@ -276,12 +276,20 @@ def workload_autograd(B, W, torch, dev, rank, log2n):
         loss = (w * Fn.sin(x) + v * Fn.cos(x) + u * torch.clamp(Fn.tan(x), -50, 50)).sum()
         loss.backward()
 
-    ks = [Kernel("loss_fwd_bwd", 4 * n * 10, n, fwd_bwd, launches=6)]
+    def fused():
+        x.grad = None
+        Fn.sincostan_loss(x, w, v, u, -50.0, 50.0).backward()
+
+    # algorithmic bytes of the unfused step: forward reads x three times and
+    # writes three outputs; backward reads x and the incoming gradient and
+    # writes a gradient for each function (the torch elementwise ops between
+    # them are not counted)
+    ks = [Kernel("loss_fwd_bwd", 4 * n * 15, n, fwd_bwd, launches=6)]
     meta = {"metric": "Gelem/s, forward + backward of sum(w sin + v cos + u clamp(tan, -50, 50)) over [8192, 4096] "
                       "fp32 (autograd.Function, hand-written derivative kernels)",
             "dtype": "f32", "workload": "differentiation: x U[-4pi, 4pi], w, v, u ~ N(0,1), [8192, 4096]",
             "n_per_gpu": n, "l2": "inputs larger than L2, no flush"}
-    return ks, meta, {}
+    return ks, meta, {"fused": fused, "n": n}
 
 
 WORKLOADS = {"bandwidth": workload_bandwidth, "half": workload_half, "large": workload_large,
@@ -403,6 +411,14 @@ def main():
         ms = _time_call(lambda: plan.run_per_array(stream.cuda_stream), 3, stream)
         line["per_array_launches"] = {"ms": round(ms, 3), "gelem_s": round(meta["n_per_gpu"] / ms / 1e6, 2),
                                       "launches": len(state["descs"])}
+    if args.workload == "autograd" and rank == 0:
+        nn = state["n"]
+        ms = _time_call(state["fused"], 5, stream)
+        line["fused_loss"] = {"ms": round(ms, 3), "gelem_s": round(nn / ms / 1e6, 2),
+                              "gb_s": round(20 * nn / ms / 1e6, 1), "hbm_frac": round(20 * nn / ms / 1e6 / peak, 4),
+                              "speedup_vs_unfused": round(ms_per_step / ms, 2),
+                              "how": "one kernel: sin, cos, tan and their derivatives from one reduction; "
+                                     "reads x, w, v, u, writes dL/dx (20 B/angle)"}
     if args.workload == "bandwidth" and not args.no_extras and rank == 0:
         line.update(extras(args, B, W, state["x"], state["x_host"], state["n"], stream, peak, kernels))
     if rank == 0:

@@ -142,6 +142,22 @@ ptrig_status ptrig_cos_bwd_f64(const double *x, const double *gy, double *gx, si
 ptrig_status ptrig_tan_bwd_f64(const double *x, const double *gy, double *gx, size_t n, ptrig_stream stream);
 
 /* ------------------------------------------------------------------------ */
+/* Fused loss and gradient (one pass over the inputs)                       */
+/* ------------------------------------------------------------------------ */
+
+/* *loss = sum_i w[i] sin(x[i]) + v[i] cos(x[i]) + u[i] clamp(tan(x[i]), lo, hi)
+ * and gx[i] = dL/dx[i] = w[i] sin'(x[i]) + v[i] cos'(x[i]) + u[i] tan'(x[i])
+ * [lo <= tan(x[i]) <= hi], with the paper's piecewise functions and their
+ * derivatives (as in the _bwd entry points) from one reduction per angle.
+ * x, w, v, u, gx: n device floats; loss: ONE device double, overwritten (the
+ * call clears it with cudaMemsetAsync, then accumulates per-block FP64 partial
+ * sums; the summation order, hence the last bits, may vary between runs).
+ * NULL pointers with n > 0, loss == NULL or lo > hi: PTRIG_ERR_INVALID_ARG. */
+ptrig_status ptrig_sincostan_loss_f32(const float *x, const float *w, const float *v, const float *u, size_t n,
+                                      float clamp_lo, float clamp_hi, double *loss, float *gx,
+                                      ptrig_stream stream);
+
+/* ------------------------------------------------------------------------ */
 /* Diagnostics                                                              */
 /* ------------------------------------------------------------------------ */
 
@@ -163,16 +179,21 @@ ptrig_status ptrig_cudamath_f32(int func, int fast, const float *x, float *y0, f
 
 /* Kernel families for ptrig_set_launch_config. */
 typedef enum ptrig_family {
-  PTRIG_FAMILY_F32 = 0,    /* proposed FP32, all functions */
-  PTRIG_FAMILY_HALF = 1,   /* f16 and bf16 storage */
-  PTRIG_FAMILY_TAYLOR = 2, /* Taylor-n FP32 */
-  PTRIG_FAMILY_BWD = 3,    /* FP32 derivatives */
-  PTRIG_FAMILY_COUNT = 4
+  PTRIG_FAMILY_F32 = 0,      /* proposed FP32, all functions */
+  PTRIG_FAMILY_HALF = 1,     /* fp16 storage */
+  PTRIG_FAMILY_TAYLOR = 2,   /* Taylor-n FP32 */
+  PTRIG_FAMILY_BWD = 3,      /* FP32 derivatives */
+  PTRIG_FAMILY_BF16 = 4,     /* bf16 storage */
+  PTRIG_FAMILY_CUDAMATH = 5, /* ptrig_cudamath_f32 comparison kernels */
+  PTRIG_FAMILY_COUNT = 6
 } ptrig_family;
 
-/* Threads per block (64..1024, multiple of 32), 16-byte vectors per thread
- * per iteration (1, 2 or 4) and the grid cap in blocks per SM (0 = one
- * block per vector group, no cap).  Process-wide; affects later launches. */
+/* Threads per block (64..512, multiple of 32), 16-byte loads kept in flight
+ * per thread (1, 2 or 4) and the grid shape: blocks_per_sm = 0 launches one
+ * block per contiguous chunk of block * vec_per_thread vectors (one-shot);
+ * blocks_per_sm = k > 0 launches a persistent grid of k blocks per SM that
+ * strides over the array.  Process-wide; affects later launches.  The
+ * defaults were measured on GB300. */
 ptrig_status ptrig_set_launch_config(int family, int block, int vec_per_thread, int blocks_per_sm);
 ptrig_status ptrig_get_launch_config(int family, int *block, int *vec_per_thread, int *blocks_per_sm);
 

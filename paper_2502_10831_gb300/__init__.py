@@ -11,4 +11,5 @@ this package is its thin Python layer:
 Nothing here computes a trigonometric value itself; without the built library
 the calls raise ImportError.
 """
-from .functional import cos, cudamath, derivative, forward, segment, sin, sincos, tan, taylor  # noqa: F401
+from .functional import (cos, cudamath, derivative, forward, segment, sin, sincos,  # noqa: F401
+                         sincostan_loss, tan, taylor)

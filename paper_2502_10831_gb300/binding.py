@@ -17,7 +17,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_build", "libptrig.so")
 
 SIN, COS, TAN, SINCOS = 0, 1, 2, 3
-FAMILY_F32, FAMILY_HALF, FAMILY_TAYLOR, FAMILY_BWD = 0, 1, 2, 3
+FAMILY_F32, FAMILY_HALF, FAMILY_TAYLOR, FAMILY_BWD, FAMILY_BF16, FAMILY_CUDAMATH = 0, 1, 2, 3, 4, 5
 BATCH_GRAPH = 1
 
 _P = ctypes.c_void_p
@@ -54,6 +54,7 @@ SIGNATURES = {
     "ptrig_sin_bwd_f64": [_P, _P, _P, _SZ, _P],
     "ptrig_cos_bwd_f64": [_P, _P, _P, _SZ, _P],
     "ptrig_tan_bwd_f64": [_P, _P, _P, _SZ, _P],
+    "ptrig_sincostan_loss_f32": [_P, _P, _P, _P, _SZ, ctypes.c_float, ctypes.c_float, _P, _P, _P],
     "ptrig_segment_f32": [_P, _P, _SZ, _P],
     "ptrig_cudamath_f32": [_I, _I, _P, _P, _P, _SZ, _P],
     "ptrig_set_launch_config": [_I, _I, _I, _I],
@@ -182,6 +183,15 @@ def ptrig_cudamath_f32(func, fast, x, y0, y1=None, n=None, stream=None):
     n = _count(x) if n is None else n
     _check(_load().ptrig_cudamath_f32(func, fast, _ptr(x), _ptr(y0), _ptr(y1), n, _stream(stream)),
            "ptrig_cudamath_f32")
+
+
+def ptrig_sincostan_loss_f32(x, w, v, u, clamp_lo, clamp_hi, loss, gx, n=None, stream=None):
+    """Fused loss sum(w sin + v cos + u clamp(tan)) into the device double
+    `loss`, and its gradient into gx.  See include/ptrig.h."""
+    n = _count(x) if n is None else n
+    _check(_load().ptrig_sincostan_loss_f32(_ptr(x), _ptr(w), _ptr(v), _ptr(u), n, clamp_lo, clamp_hi,
+                                            _ptr(loss), _ptr(gx), _stream(stream)),
+           "ptrig_sincostan_loss_f32")
 
 
 def ptrig_status_string(status: int) -> str:

@@ -66,11 +66,14 @@ int occupancy(const void *kernel, int block) {
   return nb;
 }
 
-// Defaults measured on GB300 (2^28 angles): every family runs 128 threads with
-// four 16-byte loads in flight per thread, one-shot chunks (one contiguous
-// 8 KiB block of input per block).
+// Defaults measured on GB300 (2^28 angles): the FP32, fp16, Taylor and
+// derivative kernels run 128 threads with four 16-byte loads in flight per
+// thread, one-shot (one contiguous 8 KiB chunk of input per block); bf16 and
+// CUDA's own math functions run best persistent (512 threads, 2 or 8 blocks
+// per SM).
 static std::mutex g_cfg_mu;
-static LaunchCfg g_cfg[PTRIG_FAMILY_COUNT] = {{128, 4, 0}, {128, 4, 0}, {128, 4, 0}, {128, 4, 0}};
+static LaunchCfg g_cfg[PTRIG_FAMILY_COUNT] = {{128, 4, 0}, {128, 4, 0}, {128, 4, 0},
+                                               {128, 4, 0}, {512, 1, 2}, {512, 2, 8}};
 
 LaunchCfg get_cfg(int family) {
   std::lock_guard<std::mutex> lk(g_cfg_mu);
@@ -215,6 +218,16 @@ PTRIG_BWD32(ptrig_tan_bwd_f32, OP_TAN)
 PTRIG_BWD64(ptrig_sin_bwd_f64, OP_SIN)
 PTRIG_BWD64(ptrig_cos_bwd_f64, OP_COS)
 PTRIG_BWD64(ptrig_tan_bwd_f64, OP_TAN)
+
+// ---------------------------------------------------- fused loss + gradient
+
+ptrig_status ptrig_sincostan_loss_f32(const float *x, const float *w, const float *v, const float *u, size_t n,
+                                      float clamp_lo, float clamp_hi, double *loss, float *gx, ptrig_stream stream) {
+  if (!loss) return PTRIG_ERR_INVALID_ARG;
+  if (n > 0 && (!x || !w || !v || !u || !gx)) return PTRIG_ERR_INVALID_ARG;
+  if (!(clamp_lo <= clamp_hi)) return PTRIG_ERR_INVALID_ARG;
+  return launch_loss_f32(x, w, v, u, n, clamp_lo, clamp_hi, loss, gx, PTRIG_STREAM(stream));
+}
 
 // ------------------------------------------------------------ diagnostics
 

@@ -75,13 +75,21 @@ static __device__ __noinline__ void batch_tile(const ptrig_desc d, uint64_t star
   const float *x = d.x + start;
   float *y0 = d.y0 + start;
   float *y1 = (OP == OP_SINCOS) ? d.y1 + start : nullptr;
-  uintptr_t a = (uintptr_t)x | (uintptr_t)y0;
-  if (OP == OP_SINCOS) a |= (uintptr_t)y1;
-  uint32_t done = 0;
-  if ((a & 15u) == 0) {
+  // A common offset inside the 16-byte line (arrays packed at arbitrary
+  // element offsets): peel up to three elements, then vectors.
+  const uint32_t ox = (uint32_t)((uintptr_t)x & 15u);
+  const bool same = ((uint32_t)((uintptr_t)y0 & 15u) == ox) &&
+                    (OP != OP_SINCOS || (uint32_t)((uintptr_t)y1 & 15u) == ox) && (ox & 3u) == 0;
+  uint32_t head = 0, done = 0;
+  if (same) {
+    head = ox ? (16u - ox) / 4u : 0u;
+    if (head > len) head = len;
     constexpr int U = 4;
-    const uint32_t nv = len / 4;
-    const uint4 *xv = reinterpret_cast<const uint4 *>(x);
+    const uint32_t nv = (len - head) / 4;
+    const float *xa = x + head;
+    float *y0a = y0 + head;
+    float *y1a = (OP == OP_SINCOS) ? y1 + head : nullptr;
+    const uint4 *xv = reinterpret_cast<const uint4 *>(xa);
     uint32_t resume = 0;
     for (uint32_t v0 = threadIdx.x; v0 < nv; v0 += blockDim.x * U) {
       uint4 buf[U];
@@ -93,16 +101,17 @@ static __device__ __noinline__ void batch_tile(const ptrig_desc d, uint64_t star
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const uint32_t i = v0 + u * blockDim.x;
-        if (i < nv && !map_vector_fast<float, F>(buf[u], i, y0, y1, tab)) {
+        if (i < nv && !map_vector_fast<float, F>(buf[u], i, y0a, y1a, tab)) {
           resume = i + 1;
           goto full;
         }
       }
     }
   full:
-    if (resume) batch_resume_full<OP>(x, y0, y1, resume - 1, nv, tab);
-    done = nv * 4;
+    if (resume) batch_resume_full<OP>(xa, y0a, y1a, resume - 1, nv, tab);
+    done = head + nv * 4;
   }
+  if (head > 0) batch_elements<OP>(x, y0, y1, 0, head, tab);
   if (done < len) batch_elements<OP>(x, y0, y1, done, len, tab);
 }
 

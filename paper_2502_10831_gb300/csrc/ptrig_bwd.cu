@@ -160,6 +160,174 @@ ptrig_status launch_bwd_f32(int op, const float *x, const float *gy, float *gx, 
   }
 }
 
+// ------------------------------------------------------ fused loss + gradient
+
+// One pass of  L = sum_i w_i sin(x_i) + v_i cos(x_i) + u_i clamp(tan(x_i), lo, hi)
+// and dL/dx_i with the paper's functions: one reduction and one table lookup
+// give N, D, rs = 1/h and rd = 1/D; then
+//   sin = N rs, cos = D rs, tan = N rd               (signed as in sign_bits)
+//   dsin = D Dl rs^3, dcos = -N Dl rs^3, dtan = Dl rd^2  (times s_f sign(r))
+// and the clamp passes the gradient where lo <= tan <= hi.
+template <bool FULL>
+__device__ __forceinline__ float loss_element(float x, float w, float v, float u, float lo, float hi,
+                                              const float4 *tab, float &g) {
+  const RedF red = reduce_sel<FULL>(x);
+  const float t = fabsf(red.r);
+  const float4 c = tab[table_index(t, red.jb)];
+  const float N = __fmaf_rn(c.x, t, c.y);
+  const float D = __fmaf_rn(c.z, t, c.w);
+  const float dl = __fmaf_rn(c.x, c.w, -__fmul_rn(c.y, c.z));
+  const Signs sg = sign_bits(red.jb, __float_as_uint(red.r));
+  const uint32_t sr = __float_as_uint(red.r) & 0x80000000u;
+  const float rs = rsqrt_approx(__fmaf_rn(N, N, __fmul_rn(D, D)));
+  const float rd = rcp_approx(D);
+  const float rs3 = __fmul_rn(rs, __fmul_rn(rs, rs));
+  const float sv = xor_sign(__fmul_rn(N, rs), sg.s);
+  const float cv = xor_sign(__fmul_rn(D, rs), sg.c);
+  const float tv = xor_sign(__fmul_rn(N, rd), sg.t);
+  const float ds = xor_sign(__fmul_rn(__fmul_rn(D, dl), rs3), sg.s ^ sr);
+  const float dc = xor_sign(__fmul_rn(__fmul_rn(-N, dl), rs3), sg.c ^ sr);
+  const float dt = xor_sign(__fmul_rn(dl, __fmul_rn(rd, rd)), sg.t ^ sr);
+  const bool inside = (tv >= lo) && (tv <= hi);
+  const float tc = fminf(fmaxf(tv, lo), hi);
+  g = __fmaf_rn(w, ds, __fmaf_rn(v, dc, inside ? __fmul_rn(u, dt) : 0.0f));
+  return __fmaf_rn(w, sv, __fmaf_rn(v, cv, __fmul_rn(u, tc)));
+}
+
+struct LossVec {
+  uint4 x, w, v, u;
+};
+
+__device__ __forceinline__ LossVec load_loss_vec(const float *x, const float *w, const float *v, const float *u,
+                                                 size_t i) {
+  return {ld_stream(reinterpret_cast<const uint4 *>(x) + i), ld_stream(reinterpret_cast<const uint4 *>(w) + i),
+          ld_stream(reinterpret_cast<const uint4 *>(v) + i), ld_stream(reinterpret_cast<const uint4 *>(u) + i)};
+}
+
+// One vector with the FP32 reduction: adds its loss to *acc and stores its
+// gradient; false (nothing stored) if an angle needs the full reduction.
+__device__ __forceinline__ bool loss_vector_fast(const LossVec &q, size_t i, float lo, float hi, const float4 *tab,
+                                                 float *gx, double &acc) {
+  float xf[4], wf[4], vf[4], uf[4], g[4];
+  Storage<float>::unpack(q.x, xf);
+  bool slow = false;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) slow |= needs_slow(xf[e]);
+  if (slow) return false;
+  Storage<float>::unpack(q.w, wf);
+  Storage<float>::unpack(q.v, vf);
+  Storage<float>::unpack(q.u, uf);
+  float part = 0.0f;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) part += loss_element<false>(xf[e], wf[e], vf[e], uf[e], lo, hi, tab, g[e]);
+  acc += (double)part;
+  st_stream(reinterpret_cast<uint4 *>(gx) + i, Storage<float>::pack(g));
+  return true;
+}
+
+// Remaining vectors i, i + stride, ... of a thread with the full reduction.
+static __device__ __noinline__ double loss_resume_full(const float *x, const float *w, const float *v,
+                                                       const float *u, size_t i, size_t nvec, size_t stride,
+                                                       float lo, float hi, const float4 *tab, float *gx) {
+  double acc = 0.0;
+  for (; i < nvec; i += stride) {
+    const LossVec q = load_loss_vec(x, w, v, u, i);
+    float xf[4], wf[4], vf[4], uf[4], g[4];
+    Storage<float>::unpack(q.x, xf);
+    Storage<float>::unpack(q.w, wf);
+    Storage<float>::unpack(q.v, vf);
+    Storage<float>::unpack(q.u, uf);
+    float part = 0.0f;
+    for (int e = 0; e < 4; ++e) part += loss_element<true>(xf[e], wf[e], vf[e], uf[e], lo, hi, tab, g[e]);
+    acc += (double)part;
+    st_stream(reinterpret_cast<uint4 *>(gx) + i, Storage<float>::pack(g));
+  }
+  return acc;
+}
+
+// Elements [from, n) one at a time (unaligned inputs, the n % 4 tail).
+static __device__ __noinline__ double loss_elements(const float *x, const float *w, const float *v, const float *u,
+                                                    size_t from, size_t n, size_t stride, float lo, float hi,
+                                                    const float4 *tab, float *gx) {
+  double acc = 0.0;
+  for (size_t i = from; i < n; i += stride) {
+    float g;
+    acc += (double)loss_element<true>(x[i], w[i], v[i], u[i], lo, hi, tab, g);
+    gx[i] = g;
+  }
+  return acc;
+}
+
+// Persistent grid over 16-byte vectors of x, w, v, u with a ring of two
+// vector quadruples in flight per thread (as in k_map); per-thread FP64
+// partial sums, reduced per block and added to *loss with one atomic.
+__global__ void __launch_bounds__(256) k_loss(const float *__restrict__ x, const float *__restrict__ w,
+                                              const float *__restrict__ v, const float *__restrict__ u, size_t n,
+                                              float lo, float hi, double *loss, float *__restrict__ gx) {
+  constexpr int D = 2;
+  __shared__ float4 s_tab[8];
+  __shared__ double s_sum[8];
+  if (threadIdx.x < 8) s_tab[threadIdx.x] = c_tab_f32[threadIdx.x];
+  __syncthreads();
+  double acc = 0.0;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const bool aligned = (((uintptr_t)x | (uintptr_t)w | (uintptr_t)v | (uintptr_t)u | (uintptr_t)gx) & 15u) == 0;
+  const size_t nvec = aligned ? n / 4 : 0;
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t first = i;
+  size_t resume = 0;
+  LossVec buf[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const size_t j = i + (size_t)d * stride;
+    if (j < nvec) buf[d] = load_loss_vec(x, w, v, u, j);
+  }
+  for (; i < nvec; i += (size_t)D * stride) {
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const size_t ii = i + (size_t)d * stride;
+      if (ii < nvec) {
+        const LossVec cur = buf[d];
+        const size_t jn = ii + (size_t)D * stride;
+        if (jn < nvec) buf[d] = load_loss_vec(x, w, v, u, jn);
+        if (!loss_vector_fast(cur, ii, lo, hi, s_tab, gx, acc)) {
+          resume = ii + 1;
+          goto full;
+        }
+      }
+    }
+  }
+  goto rest;
+full:
+  acc += loss_resume_full(x, w, v, u, resume - 1, nvec, stride, lo, hi, s_tab, gx);
+rest:
+  if (nvec * 4 < n) acc += loss_elements(x, w, v, u, nvec * 4 + first, n, stride, lo, hi, s_tab, gx);
+  // block sum: warp shuffles, then one double atomic per block
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) b += s_sum[k];
+    atomicAdd(loss, b);
+  }
+}
+
+ptrig_status launch_loss_f32(const float *x, const float *w, const float *v, const float *u, size_t n, float lo,
+                             float hi, double *loss, float *gx, cudaStream_t s) {
+  const int sms = sm_count();
+  if (sms <= 0) return PTRIG_ERR_NO_DEVICE;
+  cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(double), s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (n == 0) return PTRIG_OK;
+  const int occ = occupancy((const void *)k_loss, 256);
+  size_t g = (size_t)sms * (size_t)(occ > 0 ? occ : 1);
+  const size_t need = (n + 1023) / 1024;
+  if (g > need) g = need < 1 ? 1 : need;
+  k_loss<<<(unsigned)g, 256, 0, s>>>(x, w, v, u, n, lo, hi, loss, gx);
+  return finish_launch();
+}
+
 // ---------------------------------------------------------------------- FP64
 
 template <int OP, int BWD>

@@ -76,13 +76,13 @@ template <int FAST>
 static ptrig_status launch_cudamath_fast(int op, const float *x, float *y0, float *y1, size_t n, cudaStream_t s) {
   switch (op) {
     case OP_SIN:
-      return launch_map<float, CudaMath<OP_SIN, FAST>>(PTRIG_FAMILY_F32, x, y0, y1, n, s);
+      return launch_map<float, CudaMath<OP_SIN, FAST>>(PTRIG_FAMILY_CUDAMATH, x, y0, y1, n, s);
     case OP_COS:
-      return launch_map<float, CudaMath<OP_COS, FAST>>(PTRIG_FAMILY_F32, x, y0, y1, n, s);
+      return launch_map<float, CudaMath<OP_COS, FAST>>(PTRIG_FAMILY_CUDAMATH, x, y0, y1, n, s);
     case OP_TAN:
-      return launch_map<float, CudaMath<OP_TAN, FAST>>(PTRIG_FAMILY_F32, x, y0, y1, n, s);
+      return launch_map<float, CudaMath<OP_TAN, FAST>>(PTRIG_FAMILY_CUDAMATH, x, y0, y1, n, s);
     case OP_SINCOS:
-      return launch_map<float, CudaMath<OP_SINCOS, FAST>>(PTRIG_FAMILY_F32, x, y0, y1, n, s);
+      return launch_map<float, CudaMath<OP_SINCOS, FAST>>(PTRIG_FAMILY_CUDAMATH, x, y0, y1, n, s);
     default:
       return PTRIG_ERR_INVALID_ARG;
   }

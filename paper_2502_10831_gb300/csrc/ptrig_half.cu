@@ -6,31 +6,31 @@
 
 namespace ptrig {
 
-template <typename T>
+template <typename T, int FAMILY>
 static ptrig_status launch_half(int op, const void *x, void *y0, void *y1, size_t n, cudaStream_t s) {
   const T *xi = static_cast<const T *>(x);
   T *o0 = static_cast<T *>(y0);
   T *o1 = static_cast<T *>(y1);
   switch (op) {
     case OP_SIN:
-      return launch_map<T, Proposed<OP_SIN>>(PTRIG_FAMILY_HALF, xi, o0, o1, n, s);
+      return launch_map<T, Proposed<OP_SIN>>(FAMILY, xi, o0, o1, n, s);
     case OP_COS:
-      return launch_map<T, Proposed<OP_COS>>(PTRIG_FAMILY_HALF, xi, o0, o1, n, s);
+      return launch_map<T, Proposed<OP_COS>>(FAMILY, xi, o0, o1, n, s);
     case OP_TAN:
-      return launch_map<T, Proposed<OP_TAN>>(PTRIG_FAMILY_HALF, xi, o0, o1, n, s);
+      return launch_map<T, Proposed<OP_TAN>>(FAMILY, xi, o0, o1, n, s);
     case OP_SINCOS:
-      return launch_map<T, Proposed<OP_SINCOS>>(PTRIG_FAMILY_HALF, xi, o0, o1, n, s);
+      return launch_map<T, Proposed<OP_SINCOS>>(FAMILY, xi, o0, o1, n, s);
     default:
       return PTRIG_ERR_INVALID_ARG;
   }
 }
 
 ptrig_status launch_proposed_f16(int op, const void *x, void *y0, void *y1, size_t n, cudaStream_t s) {
-  return launch_half<__half>(op, x, y0, y1, n, s);
+  return launch_half<__half, PTRIG_FAMILY_HALF>(op, x, y0, y1, n, s);
 }
 
 ptrig_status launch_proposed_bf16(int op, const void *x, void *y0, void *y1, size_t n, cudaStream_t s) {
-  return launch_half<__nv_bfloat16>(op, x, y0, y1, n, s);
+  return launch_half<__nv_bfloat16, PTRIG_FAMILY_BF16>(op, x, y0, y1, n, s);
 }
 
 }  // namespace ptrig

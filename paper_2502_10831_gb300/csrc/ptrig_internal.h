@@ -31,6 +31,8 @@ ptrig_status launch_taylor_f32(int op, int nterms, const float *x, float *y, siz
 ptrig_status launch_bwd_f32(int op, const float *x, const float *gy, float *gx, size_t n, cudaStream_t s);
 ptrig_status launch_f64(int op, int bwd, const double *x, const double *gy, double *out, size_t n,
                         cudaStream_t s);
+ptrig_status launch_loss_f32(const float *x, const float *w, const float *v, const float *u, size_t n, float lo,
+                             float hi, double *loss, float *gx, cudaStream_t s);
 ptrig_status launch_segment_f32(const float *x, uint8_t *out, size_t n, cudaStream_t s);
 ptrig_status launch_cudamath_f32(int op, int fast, const float *x, float *y0, float *y1, size_t n,
                                  cudaStream_t s);

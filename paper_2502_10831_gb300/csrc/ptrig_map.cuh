@@ -206,9 +206,20 @@ ptrig_status launch_map(int family, const T *x, T *y0, T *y1, size_t n, cudaStre
   uintptr_t a = (uintptr_t)x | (uintptr_t)y0;
   if (F::NOUT == 2) a |= (uintptr_t)y1;
   if (a & 15u) {
-    const size_t blocks = grid_for(n, (size_t)c.block, LaunchCfg{c.block, 1, 16}, sms);
-    k_map_scalar<T, F><<<(unsigned)blocks, c.block, 0, s>>>(x, y0, y1, n);
-    return finish_launch();
+    // Pointers that share one offset inside a 16-byte line (an array and its
+    // output both sliced at the same element): the first `head` elements go
+    // element by element, the rest as 16-byte vectors.  Otherwise every
+    // element goes element by element.
+    const uintptr_t ox = (uintptr_t)x & 15u;
+    const bool same = ((uintptr_t)y0 & 15u) == ox && (F::NOUT == 1 || ((uintptr_t)y1 & 15u) == ox) &&
+                      ox % sizeof(T) == 0;
+    size_t head = same ? (16u - ox) / sizeof(T) : n;
+    if (head > n) head = n;
+    const size_t blocks = grid_for(head, (size_t)c.block, LaunchCfg{c.block, 1, 16}, sms);
+    k_map_scalar<T, F><<<(unsigned)blocks, c.block, 0, s>>>(x, y0, y1, head);
+    const ptrig_status st = finish_launch();
+    if (st != PTRIG_OK || head == n) return st;
+    return launch_map<T, F>(family, x + head, y0 + head, F::NOUT == 2 ? y1 + head : y1, n - head, s);
   }
   switch (c.vpt) {
     case 1:

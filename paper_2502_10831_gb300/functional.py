@@ -107,3 +107,32 @@ def cudamath(func: str, x: torch.Tensor, fast: bool = False):
         return y0, y1
     B.ptrig_cudamath_f32(_FUNCS.index(func), int(fast), x, y0)
     return y0
+
+
+class _FusedLoss(torch.autograd.Function):
+    """L = sum(w sin(x) + v cos(x) + u clamp(tan(x), lo, hi)) and dL/dx from one
+    kernel pass; the gradient is kept for backward.  w, v, u are constants."""
+
+    @staticmethod
+    def forward(ctx, x, w, v, u, lo, hi):
+        x, w, v, u = (t.contiguous() for t in (x, w, v, u))
+        loss = torch.empty((), dtype=torch.float64, device=x.device)
+        gx = torch.empty_like(x)
+        B.ptrig_sincostan_loss_f32(x, w, v, u, float(lo), float(hi), loss, gx)
+        ctx.save_for_backward(gx)
+        return loss.to(x.dtype)
+
+    @staticmethod
+    def backward(ctx, g):
+        (gx,) = ctx.saved_tensors
+        return g.to(gx.dtype) * gx, None, None, None, None, None
+
+
+def sincostan_loss(x: torch.Tensor, w: torch.Tensor, v: torch.Tensor, u: torch.Tensor,
+                   lo: float = -50.0, hi: float = 50.0) -> torch.Tensor:
+    """Fused sum(w sin(x) + v cos(x) + u clamp(tan(x), lo, hi)) for float32 CUDA
+    tensors of one shape, differentiable in x."""
+    for t in (x, w, v, u):
+        if not t.is_cuda or t.dtype != torch.float32 or t.shape != x.shape:
+            raise TypeError("sincostan_loss takes float32 CUDA tensors of one shape")
+    return _FusedLoss.apply(x, w, v, u, lo, hi)
