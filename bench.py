@@ -34,6 +34,8 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_2502_10831_gb300 import replicas as R  # noqa: E402
+
 METRIC = "Gelem/s & % HBM peak, π/12 sin/cos/tan on 2^28 fp32; packed-half vs plain"
 WORKLOAD = ("bandwidth: 2^28 fp32 angles, 80% U[-100pi,100pi], 10% within 1e-4 of k*pi/12, "
             "10% within 1e-3 of odd multiples of pi/2; step = proposed sin, cos, tan, sincos + "
@@ -188,7 +190,7 @@ class Kernel:
 
 def workload_bandwidth(B, W, torch, dev, rank, log2n):
     n = 1 << log2n
-    x_host = W.bandwidth(n, seed=W.SEED + rank)
+    x_host = W.bandwidth(n, seed=R.shard_seed(W.SEED, rank))
     x = torch.from_numpy(x_host).to(dev)
     o = [torch.empty_like(x) for _ in range(2)]
     s = torch.cuda.current_stream().cuda_stream
@@ -207,8 +209,8 @@ def workload_bandwidth(B, W, torch, dev, rank, log2n):
 def workload_half(B, W, torch, dev, rank, log2n):
     import numpy as np
     n = 1 << log2n
-    xs = {"f16": torch.from_numpy(W.half16(n, seed=W.SEED + rank).view(np.int16)).to(dev),
-          "bf16": torch.from_numpy(W.half_bf16(n, seed=W.SEED + rank).view(np.int16)).to(dev)}
+    xs = {"f16": torch.from_numpy(W.half16(n, seed=R.shard_seed(W.SEED, rank)).view(np.int16)).to(dev),
+          "bf16": torch.from_numpy(W.half_bf16(n, seed=R.shard_seed(W.SEED, rank)).view(np.int16)).to(dev)}
     o = [torch.empty_like(xs["f16"]) for _ in range(2)]
     s = torch.cuda.current_stream().cuda_stream
     ks = []
@@ -226,7 +228,7 @@ def workload_half(B, W, torch, dev, rank, log2n):
 
 def workload_large(B, W, torch, dev, rank, log2n):
     n = 1 << min(log2n, 24)
-    x = torch.from_numpy(W.large(n, seed=W.SEED + rank)).to(dev)
+    x = torch.from_numpy(W.large(n, seed=R.shard_seed(W.SEED, rank))).to(dev)
     o = [torch.empty_like(x) for _ in range(2)]
     s = torch.cuda.current_stream().cuda_stream
     ks = [Kernel("sin_f32", 8 * n, n, lambda: B.ptrig_sin_f32(x, o[0], n, s)),
@@ -242,7 +244,7 @@ def workload_large(B, W, torch, dev, rank, log2n):
 
 
 def workload_batch(B, W, torch, dev, rank, log2n):
-    lengths, sel = W.batch_spec(4096, seed=W.SEED + rank)
+    lengths, sel = W.batch_spec(4096, seed=R.shard_seed(W.SEED, rank))
     total = int(lengths.sum())
     padded = int(sum((int(n) + 63) // 64 * 64 for n in lengths))
     xs = torch.empty(padded, dtype=torch.float32, device=dev)
@@ -251,7 +253,7 @@ def workload_batch(B, W, torch, dev, rank, log2n):
     descs, off, nbytes = [], 0, 0
     for i, (n, f) in enumerate(zip(lengths, sel)):
         n = int(n)
-        xs[off:off + n] = torch.from_numpy(W.batch_array(i, n, seed=W.SEED + rank)).to(dev)
+        xs[off:off + n] = torch.from_numpy(W.batch_array(i, n, seed=R.shard_seed(W.SEED, rank))).to(dev)
         descs.append((xs[off:off + n], y0[off:off + n], y1[off:off + n] if f == 3 else None, n, int(f)))
         nbytes += (12 if f == 3 else 8) * n
         off += (n + 63) // 64 * 64  # each array starts on a 256-byte boundary, as separate allocations would
@@ -269,7 +271,7 @@ def workload_batch(B, W, torch, dev, rank, log2n):
 
 def workload_autograd(B, W, torch, dev, rank, log2n):
     from paper_2502_10831_gb300 import functional as Fn
-    x_h, w_h, v_h, u_h = W.autograd((8192, 4096), seed=W.SEED + rank)
+    x_h, w_h, v_h, u_h = W.autograd((8192, 4096), seed=R.shard_seed(W.SEED, rank))
     x = torch.from_numpy(x_h).to(dev).requires_grad_(True)
     w, v, u = (torch.from_numpy(a).to(dev) for a in (w_h, v_h, u_h))
     n = x.numel()
@@ -312,9 +314,7 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = R.rank_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
 
@@ -367,16 +367,11 @@ def main():
     if dist:
         dist.barrier()
     clk = clocks.stop(wall0, wall0 + wall)
-    total_ms = t0.elapsed_time(t1)
-    if dist:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = R.max_over_ranks(t0.elapsed_time(t1), dist, dev)
     per_kernel_ms = [statistics.mean(ev[s][k].elapsed_time(ev[s][k + 1]) for s in range(args.steps))
                      for k in range(nk)]
     ms_per_step = total_ms / args.steps
-    evals = sum(k.elems for k in kernels_list) * world
-    value = evals / (ms_per_step * 1e-3) / 1e9
+    value = R.job_throughput(sum(k.elems for k in kernels_list), world, ms_per_step * 1e-3) / 1e9
     peak, peak_kind = _peaks()
     kernels = {}
     for kern, ms in zip(kernels_list, per_kernel_ms):

@@ -158,6 +158,20 @@ ptrig_status ptrig_sincostan_loss_f32(const float *x, const float *w, const floa
                                       ptrig_stream stream);
 
 /* ------------------------------------------------------------------------ */
+/* Paper-faithful mode (Algorithms 1-6 as printed), FP64                    */
+/* ------------------------------------------------------------------------ */
+
+/* y[i] = the paper's own implementation of sin / cos / tan (func PTRIG_SIN,
+ * PTRIG_COS or PTRIG_TAN) at x[i]: the same reduction, then the fast inverse
+ * square root of Algorithm 1 (magic 0x5fe6eb50c7b537a9, one Newton step) in
+ * place of 1/sqrt and of the reciprocal (tan = poly * FISR(c u + d)^2,
+ * Algorithm 4), the selector floor(u / 0.261) of Algorithms 5-6 (clamped to
+ * segment 5), and tan = +infinity when |u - pi/2| < 1e-3 (Algorithm 6).
+ * Reproduces the error figures of Tables 1-3; the main entry points are more
+ * accurate.  x, y: n doubles.  Bad func: PTRIG_ERR_INVALID_ARG. */
+ptrig_status ptrig_faithful_f64(int func, const double *x, double *y, size_t n, ptrig_stream stream);
+
+/* ------------------------------------------------------------------------ */
 /* Diagnostics                                                              */
 /* ------------------------------------------------------------------------ */
 

@@ -55,6 +55,7 @@ SIGNATURES = {
     "ptrig_cos_bwd_f64": [_P, _P, _P, _SZ, _P],
     "ptrig_tan_bwd_f64": [_P, _P, _P, _SZ, _P],
     "ptrig_sincostan_loss_f32": [_P, _P, _P, _P, _SZ, ctypes.c_float, ctypes.c_float, _P, _P, _P],
+    "ptrig_faithful_f64": [_I, _P, _P, _SZ, _P],
     "ptrig_segment_f32": [_P, _P, _SZ, _P],
     "ptrig_cudamath_f32": [_I, _I, _P, _P, _P, _SZ, _P],
     "ptrig_set_launch_config": [_I, _I, _I, _I],
@@ -177,6 +178,12 @@ def ptrig_taylor_n_f32(func, nterms, x, y, n=None, stream=None):
     n = _count(x) if n is None else n
     _check(_load().ptrig_taylor_n_f32(func, nterms, _ptr(x), _ptr(y), n, _stream(stream)),
            "ptrig_taylor_n_f32")
+
+
+def ptrig_faithful_f64(func, x, y, n=None, stream=None):
+    """The paper's Algorithms 1-6 (FISR, 0.261 selector, pole guard) in FP64."""
+    n = _count(x) if n is None else n
+    _check(_load().ptrig_faithful_f64(func, _ptr(x), _ptr(y), n, _stream(stream)), "ptrig_faithful_f64")
 
 
 def ptrig_cudamath_f32(func, fast, x, y0, y1=None, n=None, stream=None):

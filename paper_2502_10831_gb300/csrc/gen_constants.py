@@ -177,6 +177,18 @@ def main() -> str:
         w(f"  {lit64(f64(aN))}, {lit64(f64(bN))}, {lit64(f64(aD))}, {lit64(f64(bD))}{sep} /* seg {k} */ \\")
     w("")
 
+    # ---- u-form FP64 coefficients for the paper-faithful kernels
+    w("/* Sec. 2 formulas in the paper's variable u for segments 0..5:")
+    w(" * {a, b, c, d} = {A R, B, C R, D}, then the sin/cos radicand coefficients")
+    w(" * {x, y, z} = {a^2 + c^2, 2(ab + cd), b^2 + d^2} (appendix A.4). */")
+    w("#define PTRIG_UFORM_F64 \\")
+    for k, (A, B, C, D) in enumerate(Q):
+        a, b, c, d = A * R, Fraction(B), C * R, Fraction(D)
+        vals = [a, b, c, d, a * a + c * c, 2 * (a * b + c * d), b * b + d * d]
+        sep = "," if k < 5 else ""
+        w("  " + ", ".join(lit64(f64(v)) for v in vals) + sep + " \\")
+    w("")
+
     # ---- Taylor coefficients (Horner in u^2)
     sin_c = [Fraction((-1) ** i, math.factorial(2 * i + 1)) for i in range(9)]
     cos_c = [Fraction((-1) ** i, math.factorial(2 * i)) for i in range(9)]

@@ -229,6 +229,15 @@ ptrig_status ptrig_sincostan_loss_f32(const float *x, const float *w, const floa
   return launch_loss_f32(x, w, v, u, n, clamp_lo, clamp_hi, loss, gx, PTRIG_STREAM(stream));
 }
 
+// ------------------------------------------------------- paper-faithful mode
+
+ptrig_status ptrig_faithful_f64(int func, const double *x, double *y, size_t n, ptrig_stream stream) {
+  if (func < PTRIG_SIN || func > PTRIG_TAN) return PTRIG_ERR_INVALID_ARG;
+  if (n == 0) return PTRIG_OK;
+  if (!x || !y) return PTRIG_ERR_INVALID_ARG;
+  return launch_faithful_f64(func, x, y, n, PTRIG_STREAM(stream));
+}
+
 // ------------------------------------------------------------ diagnostics
 
 ptrig_status ptrig_segment_f32(const float *x, uint8_t *out, size_t n, ptrig_stream stream) {

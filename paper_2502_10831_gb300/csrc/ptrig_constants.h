@@ -63,6 +63,17 @@
   -0x1.1e7a9907e593bp+9, 0x1.1740000000000p+10, 0x1.746c2d5710d99p+9, 0x1.4800000000000p+6, /* seg 3 */ \
   -0x1.57c6513cad17ap+8, 0x1.2500000000000p+9, 0x1.1e7a9907e593bp+8, 0x1.6c00000000000p+6 /* seg 2 */ \
 
+/* Sec. 2 formulas in the paper's variable u for segments 0..5:
+ * {a, b, c, d} = {A R, B, C R, D}, then the sin/cos radicand coefficients
+ * {x, y, z} = {a^2 + c^2, 2(ab + cd), b^2 + d^2} (appendix A.4). */
+#define PTRIG_UFORM_F64 \
+  0x1.3b2075224955ap+9, 0.0, -0x1.ca5dc1a63c1f8p+5, 0x1.3c00000000000p+9, 0x1.871d97fb1bb7ep+18, -0x1.1ae5dd84991b7p+16, 0x1.8610000000000p+18, \
+  0x1.1e7a9907e593bp+9, 0x1.4000000000000p+3, -0x1.ca5dc1a63c1f8p+7, 0x1.4880000000000p+9, 0x1.73e16257ad3d8p+18, -0x1.1ae5dd84991b7p+18, 0x1.a5a1400000000p+18, \
+  0x1.57c6513cad17ap+8, 0x1.7000000000000p+5, -0x1.1e7a9907e593bp+8, 0x1.0e80000000000p+9, 0x1.871d97fb1bb7ep+17, -0x1.0fd1b96664877p+18, 0x1.1fe3400000000p+18, \
+  0x1.1e7a9907e593bp+9, 0x1.b200000000000p+7, -0x1.746c2d5710d99p+9, 0x1.3900000000000p+10, 0x1.af305d0f9736cp+19, -0x1.8aa2c88187338p+20, 0x1.8a30100000000p+20, \
+  0x1.ca5dc1a63c1f8p+7, 0x1.2900000000000p+8, -0x1.1e7a9907e593bp+9, 0x1.c700000000000p+9, 0x1.73e16257ad3d8p+18, -0x1.bab30d47cd917p+19, 0x1.bf6aa00000000p+19, \
+  0x1.ca5dc1a63c1f8p+5, 0x1.0f00000000000p+9, -0x1.3b2075224955ap+9, 0x1.ef00000000000p+9, 0x1.871d97fb1bb7ep+18, -0x1.2180173eae192p+20, 0x1.3700800000000p+20 \
+
 #define PTRIG_TAYLOR_SIN_F32 0x1.0000000000000p+0f, -0x1.5555560000000p-3f, 0x1.1111120000000p-7f, -0x1.a01a020000000p-13f, 0x1.71de3a0000000p-19f, -0x1.ae64560000000p-26f, 0x1.6124620000000p-33f, -0x1.ae7f3e0000000p-41f, 0x1.952c780000000p-49f
 #define PTRIG_TAYLOR_SIN_F64 0x1.0000000000000p+0, -0x1.5555555555555p-3, 0x1.1111111111111p-7, -0x1.a01a01a01a01ap-13, 0x1.71de3a556c734p-19, -0x1.ae64567f544e4p-26, 0x1.6124613a86d09p-33, -0x1.ae7f3e733b81fp-41, 0x1.952c77030ad4ap-49
 #define PTRIG_TAYLOR_COS_F32 0x1.0000000000000p+0f, -0x1.0000000000000p-1f, 0x1.5555560000000p-5f, -0x1.6c16c20000000p-10f, 0x1.a01a020000000p-16f, -0x1.27e4fc0000000p-22f, 0x1.1eed8e0000000p-29f, -0x1.93974a0000000p-37f, 0x1.ae7f3e0000000p-45f

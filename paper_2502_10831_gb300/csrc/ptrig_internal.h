@@ -33,6 +33,7 @@ ptrig_status launch_f64(int op, int bwd, const double *x, const double *gy, doub
                         cudaStream_t s);
 ptrig_status launch_loss_f32(const float *x, const float *w, const float *v, const float *u, size_t n, float lo,
                              float hi, double *loss, float *gx, cudaStream_t s);
+ptrig_status launch_faithful_f64(int op, const double *x, double *y, size_t n, cudaStream_t s);
 ptrig_status launch_segment_f32(const float *x, uint8_t *out, size_t n, cudaStream_t s);
 ptrig_status launch_cudamath_f32(int op, int fast, const float *x, float *y0, float *y1, size_t n,
                                  cudaStream_t s);
