@@ -203,7 +203,8 @@ typedef enum ptrig_family {
 } ptrig_family;
 
 /* Threads per block (64..512, multiple of 32), 16-byte loads kept in flight
- * per thread (1, 2 or 4) and the grid shape: blocks_per_sm = 0 launches one
+ * per thread (1, 2, 4, or 8 for fp16 / bf16; 8 acts as 4 for 4-byte types)
+ * and the grid shape: blocks_per_sm = 0 launches one
  * block per contiguous chunk of block * vec_per_thread vectors (one-shot);
  * blocks_per_sm = k > 0 launches a persistent grid of k blocks per SM that
  * strides over the array.  Process-wide; affects later launches.  The

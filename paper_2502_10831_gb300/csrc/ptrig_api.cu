@@ -66,14 +66,14 @@ int occupancy(const void *kernel, int block) {
   return nb;
 }
 
-// Defaults measured on GB300 (2^28 angles): the FP32, fp16, Taylor and
+// Defaults measured on GB300 (2^28 angles): the FP32, bf16, Taylor and
 // derivative kernels run 128 threads with four 16-byte loads in flight per
-// thread, one-shot (one contiguous 8 KiB chunk of input per block); bf16 and
-// CUDA's own math functions run best persistent (512 threads, 2 or 8 blocks
-// per SM).
+// thread, one-shot (one contiguous 8 KiB chunk of input per block); fp16 the
+// same with eight loads in flight; CUDA's own math functions run best
+// persistent (512 threads, 8 blocks per SM).
 static std::mutex g_cfg_mu;
-static LaunchCfg g_cfg[PTRIG_FAMILY_COUNT] = {{128, 4, 0}, {128, 4, 0}, {128, 4, 0},
-                                               {128, 4, 0}, {512, 1, 2}, {512, 2, 8}};
+static LaunchCfg g_cfg[PTRIG_FAMILY_COUNT] = {{128, 4, 0}, {128, 8, 0}, {128, 4, 0},
+                                               {128, 4, 0}, {128, 4, 0}, {512, 2, 8}};
 
 LaunchCfg get_cfg(int family) {
   std::lock_guard<std::mutex> lk(g_cfg_mu);
@@ -81,7 +81,8 @@ LaunchCfg get_cfg(int family) {
 }
 
 static bool valid_cfg(int block, int vpt, int bps) {
-  return block >= 64 && block <= 512 && block % 32 == 0 && (vpt == 1 || vpt == 2 || vpt == 4) && bps >= 0 &&
+  return block >= 64 && block <= 512 && block % 32 == 0 && (vpt == 1 || vpt == 2 || vpt == 4 || vpt == 8) &&
+         bps >= 0 &&
          bps <= 64;
 }
 

@@ -501,7 +501,9 @@ template <>
 struct Storage<__nv_bfloat16> {
   static constexpr int EPV = 8;
   __device__ __forceinline__ static float2 to_float2(uint32_t w) {
-    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+    __nv_bfloat162 h;
+    *reinterpret_cast<uint32_t *>(&h) = w;
+    return __bfloat1622float2(h);
   }
   __device__ __forceinline__ static uint32_t from_float2(float2 v) {
     const __nv_bfloat162 h = __float22bfloat162_rn(v);

@@ -96,8 +96,15 @@ static __device__ __noinline__ void map_resume_full(const T *__restrict__ x, T *
 //     a grid of a few blocks per SM walks the whole array.
 //   one-shot   (PERSIST = false): base = b*B*D + t, step = B, end = base + D*B;
 //     each block streams one contiguous chunk of D*B vectors and retires.
+// Single-output functions on 16-bit storage are instruction-bound: their
+// registers are capped at 64 (two 512-thread blocks per SM) for more resident
+// warps.  FP32 is memory-bound and sincos would spill, so both keep the
+// compiler's choice.
+template <typename T, class F>
+constexpr int map_min_blocks() { return (sizeof(T) == 2 && F::NOUT == 1) ? 2 : 1; }
+
 template <typename T, class F, int D, bool PERSIST>
-__global__ void __launch_bounds__(512) k_map(const T *__restrict__ x, T *__restrict__ y0, T *__restrict__ y1,
+__global__ void __launch_bounds__(512, map_min_blocks<T, F>()) k_map(const T *__restrict__ x, T *__restrict__ y0, T *__restrict__ y1,
                                              size_t n) {
   __shared__ float4 s_tab[8];
   if (threadIdx.x < 8) s_tab[threadIdx.x] = c_tab_f32[threadIdx.x];
@@ -226,6 +233,9 @@ ptrig_status launch_map(int family, const T *x, T *y0, T *y1, size_t n, cudaStre
       return launch_map_d<T, F, 1>(c, sms, x, y0, y1, n, s);
     case 2:
       return launch_map_d<T, F, 2>(c, sms, x, y0, y1, n, s);
+    case 8:
+      if constexpr (sizeof(T) == 2) return launch_map_d<T, F, 8>(c, sms, x, y0, y1, n, s);
+      return launch_map_d<T, F, 4>(c, sms, x, y0, y1, n, s);
     default:
       return launch_map_d<T, F, 4>(c, sms, x, y0, y1, n, s);
   }

@@ -69,6 +69,7 @@ def test_host_validation_without_gpu(lib):
     assert lib.ptrig_set_launch_config(0, 100, 4, 0) == 1
     assert lib.ptrig_set_launch_config(0, 256, 3, 0) == 1
     assert lib.ptrig_set_launch_config(7, 256, 4, 0) == 1
+    assert lib.ptrig_set_launch_config(0, 256, 16, 0) == 1
 
 
 def test_launch_config_roundtrip(lib):
@@ -77,6 +78,16 @@ def test_launch_config_roundtrip(lib):
     B.ptrig_set_launch_config(B.FAMILY_TAYLOR, 128, 2, 4)
     assert B.ptrig_get_launch_config(B.FAMILY_TAYLOR) == (128, 2, 4)
     B.ptrig_set_launch_config(B.FAMILY_TAYLOR, *old)
+
+
+def test_default_launch_configs(lib):
+    """The per-family defaults picked by the GB300 sweeps (fp16 with eight
+    16-byte loads in flight, the other streaming families with four)."""
+    from paper_2502_10831_gb300 import binding as B
+    assert B.ptrig_get_launch_config(B.FAMILY_F32) == (128, 4, 0)
+    assert B.ptrig_get_launch_config(B.FAMILY_HALF) == (128, 8, 0)
+    assert B.ptrig_get_launch_config(B.FAMILY_BF16) == (128, 4, 0)
+    assert B.ptrig_get_launch_config(B.FAMILY_CUDAMATH) == (512, 2, 8)
 
 
 def test_batch_plan_rejects_bad_descriptors(lib):
