@@ -227,7 +227,7 @@ def workload_half(B, W, torch, dev, rank, log2n):
 
 
 def workload_large(B, W, torch, dev, rank, log2n):
-    n = 1 << min(log2n, 24)
+    n = 1 << min(log2n, 26)
     x = torch.from_numpy(W.large(n, seed=R.shard_seed(W.SEED, rank))).to(dev)
     o = [torch.empty_like(x) for _ in range(2)]
     s = torch.cuda.current_stream().cuda_stream
@@ -235,12 +235,14 @@ def workload_large(B, W, torch, dev, rank, log2n):
           Kernel("cos_f32", 8 * n, n, lambda: B.ptrig_cos_f32(x, o[0], n, s)),
           Kernel("tan_f32", 8 * n, n, lambda: B.ptrig_tan_f32(x, o[0], n, s)),
           Kernel("sincos_f32", 12 * n, n, lambda: B.ptrig_sincos_f32(x, o[0], o[1], n, s))]
-    meta = {"metric": "Gelem/s, pi/12 sin/cos/tan/sincos on 2^24 fp32 angles with |x| log-uniform in [1, 1e5]",
-            "dtype": "f32 (FP64 reduction above 2^10 pi)",
-            "workload": "precision: 2^24 fp32, |x| log-uniform in [1, 1e5], random sign (about 30% take the FP64 "
-                        "Cody-Waite side path)", "n_per_gpu": n,
-            "l2": "64 MiB input, smaller than L2: compute-bound (FP64 side path), no flush"}
-    return ks, meta, {}
+    meta = {"metric": f"Gelem/s, pi/12 sin/cos/tan/sincos on 2^{n.bit_length() - 1} fp32 angles with |x| "
+                      "log-uniform in [1, 1e5]",
+            "dtype": "f32 (FP64 reduction above 2^20)",
+            "workload": f"precision: 2^{n.bit_length() - 1} fp32 (the 2^24-angle precision mixture drawn at 4x the "
+                        "size so the arrays exceed L2), |x| log-uniform in [1, 1e5], random sign; all within the "
+                        "FP32 reduction range", "n_per_gpu": n,
+            "l2": "inputs larger than L2 (256 MiB vs 129 MB), no flush"}
+    return ks, meta, {"n": n}
 
 
 def workload_batch(B, W, torch, dev, rank, log2n):
@@ -294,7 +296,14 @@ def workload_autograd(B, W, torch, dev, rank, log2n):
                       "fp32 (autograd.Function, hand-written derivative kernels)",
             "dtype": "f32", "workload": "differentiation: x U[-4pi, 4pi], w, v, u ~ N(0,1), [8192, 4096]",
             "n_per_gpu": n, "l2": "inputs larger than L2, no flush"}
-    return ks, meta, {"fused": fused, "n": n}
+    loss_buf = torch.empty((), dtype=torch.float64, device=dev)
+    gx_buf = torch.empty_like(x)
+
+    def fused_kernel():
+        B.ptrig_sincostan_loss_f32(x.detach(), w, v, u, -50.0, 50.0, loss_buf, gx_buf, n,
+                                   torch.cuda.current_stream().cuda_stream)
+
+    return ks, meta, {"fused": fused, "fused_kernel": fused_kernel, "n": n}
 
 
 WORKLOADS = {"bandwidth": workload_bandwidth, "half": workload_half, "large": workload_large,
@@ -412,11 +421,18 @@ def main():
     if args.workload == "autograd" and rank == 0:
         nn = state["n"]
         ms = _time_call(state["fused"], 5, stream)
+        kms = _time_call(state["fused_kernel"], 20, stream)
         line["fused_loss"] = {"ms": round(ms, 3), "gelem_s": round(nn / ms / 1e6, 2),
-                              "gb_s": round(20 * nn / ms / 1e6, 1), "hbm_frac": round(20 * nn / ms / 1e6 / peak, 4),
                               "speedup_vs_unfused": round(ms_per_step / ms, 2),
-                              "how": "one kernel: sin, cos, tan and their derivatives from one reduction; "
-                                     "reads x, w, v, u, writes dL/dx (20 B/angle)"}
+                              "kernel_ms": round(kms, 4), "kernel_gelem_s": round(nn / kms / 1e6, 2),
+                              "kernel_gb_s": round(20 * nn / kms / 1e6, 1),
+                              "kernel_hbm_frac": round(20 * nn / kms / 1e6 / peak, 4),
+                              "how": "autograd step: one kernel computes the loss and dL/dx (sin, cos, tan and "
+                                     "their derivatives from one reduction; reads x, w, v, u, writes dL/dx, "
+                                     "20 B/angle), then backward scales dL/dx by the incoming gradient (a torch "
+                                     "multiply, 8 B/angle); kernel_* times the library call alone"}
+    if args.workload == "large" and rank == 0:
+        line["side_paths"] = side_paths(B, torch, dev, stream, peak)
     if args.workload == "bandwidth" and not args.no_extras and rank == 0:
         line.update(extras(args, B, W, state["x"], state["x_host"], state["n"], stream, peak, kernels))
     if rank == 0:
@@ -425,6 +441,26 @@ def main():
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def side_paths(B, torch, dev, stream, peak):
+    """sin_f32 throughput of the two reduction side paths on 2^26 angles each:
+    |x| log-uniform in [2^20, 2^31) (FP64 Cody-Waite) and in [2^31, 2^127]
+    (Payne-Hanek)."""
+    import numpy as np
+    n = 1 << 26
+    out = {}
+    for name, lo, hi in (("fp64_cody_waite", 20.0, 31.0), ("payne_hanek", 31.0, 127.0)):
+        r = np.random.default_rng(7)
+        xh = (2.0 ** r.uniform(lo, hi, n) * r.choice([-1.0, 1.0], n)).astype(np.float32)
+        xh = np.clip(xh, -np.float32(2.0 ** hi), np.float32(2.0 ** hi))
+        x = torch.from_numpy(xh).to(dev)
+        y = torch.empty_like(x)
+        ms = _time_call(lambda: B.ptrig_sin_f32(x, y, n, stream.cuda_stream), 5, stream)
+        out[name] = {"range": f"|x| log-uniform in [2^{lo:g}, 2^{hi:g})", "ms": round(ms, 3),
+                     "gelem_s": round(n / ms / 1e6, 2), "hbm_frac": round(8 * n / ms / 1e6 / peak, 4)}
+        del x, y
+    return out
 
 
 def _time_call(fn, reps, stream):

@@ -8,8 +8,9 @@ Cody-Waite split needs trailing zero bits).  pi comes from the Gauss-Legendre
 (Brent-Salamin) AGM iteration in fixed point.
 
 Constants
-  * Cody-Waite splits of pi/2 (Cody & Waite 1980): FP32 12+24+24 bits for
-    |x| <= 2^10 pi, FP64 21+53+53 bits for |x| < 2^31.
+  * Cody-Waite splits of pi/2 (Cody & Waite 1980): FP32 24+24+24 bits
+    (three positive floats, used with FMA) for |x| <= 2^20, FP64 21+53+53
+    bits for |x| < 2^31.
   * 2/pi as 32-bit words for the Payne-Hanek reduction of larger |x|
     (Payne & Hanek 1983).
   * The pi/12 coefficient table of the paper's Sec. 2 formulas in the
@@ -98,11 +99,18 @@ def main() -> str:
     w("#include <stdint.h>")
     w("")
 
-    # ---- FP32 Cody-Waite (|j| <= 2048: 12-bit head keeps j * P1 exact)
-    p1 = _round_bits(HALF_PI, 12, "trunc")
+    # ---- FP32 Cody-Waite with FMA (|x| <= 2^20, |j| < 2^20)
+    # P1 = pi/2 truncated to 24 bits has ulp 2^-23, so x - j P1 (one FMA) has
+    # no bit below 2^-24 and magnitude < 1 for |x| <= 2^20: it is exact.  P2
+    # (truncated) and P3 (nearest) carry the next 48 bits; the rounding of the
+    # two later FMAs and the dropped tail give |error| <= 2^-23 |r| + 2^-49.65,
+    # and no float in (0.5, 2^20] lies closer than 2^-27.8 to a multiple of
+    # pi/2.  All three pieces are positive, so x = -0 keeps its sign.
+    p1 = _round_bits(HALF_PI, 24, "trunc")
     p2 = _round_bits(HALF_PI - p1, 24, "trunc")
     p3 = _round_bits(HALF_PI - p1 - p2, 24)
-    w("/* pi/2 = PIO2_F1 + PIO2_F2 + PIO2_F3 (+ ~2^-60): 12 + 24 + 24 bits */")
+    assert p1 > 0 and p2 > 0 and p3 > 0
+    w("/* pi/2 = PIO2_F1 + PIO2_F2 + PIO2_F3 (+ < 2^-70): three positive 24-bit floats, used with FMA */")
     w(f"#define PTRIG_PIO2_F1 {lit32(float(p1))}")
     w(f"#define PTRIG_PIO2_F2 {lit32(float(p2))}")
     w(f"#define PTRIG_PIO2_F3 {lit32(float(p3))}")
@@ -111,9 +119,8 @@ def main() -> str:
     w(f"#define PTRIG_PIO2_F {lit32(f32(HALF_PI))}")
     w("/* 1.5 * 2^23: adding it rounds a float to an integer held in the low mantissa bits */")
     w(f"#define PTRIG_RINT_MAGIC_F {lit32(1.5 * 2.0 ** 23)}")
-    lim = f32(1024 * PI, "trunc")
-    w("/* largest float <= 2^10 pi: FP32 reduction bound (FP64 or Payne-Hanek above) */")
-    w(f"#define PTRIG_FAST_LIMIT_F {lit32(lim)}")
+    w("/* FP32 reduction bound 2^20 (FP64 Cody-Waite or Payne-Hanek above) */")
+    w(f"#define PTRIG_FAST_LIMIT_F {lit32(2.0 ** 20)}")
     w("")
 
     # ---- FP64 Cody-Waite (|j| < 2^31)

@@ -36,7 +36,7 @@ namespace ptrig {
 static_assert(sizeof(ptrig_desc) == 40, "ptrig_desc layout");
 
 // Vectors v, v + blockDim, ... < nv of one tile with the full reduction (out
-// of line; reached only when the tile holds an angle beyond 2^10 pi).
+// of line; reached only when the tile holds an angle beyond 2^20).
 template <int OP>
 static __device__ __noinline__ void batch_resume_full(const float *x, float *y0, float *y1, uint32_t v,
                                                       uint32_t nv, const float4 *tab) {

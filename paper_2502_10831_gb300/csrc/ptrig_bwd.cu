@@ -198,6 +198,21 @@ struct LossVec {
   uint4 x, w, v, u;
 };
 
+// Running float sum kept as hi + lo with Knuth's TwoSum (six rounded adds, no
+// contraction): lo collects each addition's rounding error, so a thread's
+// partial sum costs no FP64 work in the streaming loop.
+struct FSum {
+  float hi = 0.0f, lo = 0.0f;
+  __device__ __forceinline__ void add(float b) {
+    const float s = __fadd_rn(hi, b);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 __device__ __forceinline__ LossVec load_loss_vec(const float *x, const float *w, const float *v, const float *u,
                                                  size_t i) {
   return {ld_stream(reinterpret_cast<const uint4 *>(x) + i), ld_stream(reinterpret_cast<const uint4 *>(w) + i),
@@ -207,7 +222,7 @@ __device__ __forceinline__ LossVec load_loss_vec(const float *x, const float *w,
 // One vector with the FP32 reduction: adds its loss to *acc and stores its
 // gradient; false (nothing stored) if an angle needs the full reduction.
 __device__ __forceinline__ bool loss_vector_fast(const LossVec &q, size_t i, float lo, float hi, const float4 *tab,
-                                                 float *gx, double &acc) {
+                                                 float *gx, FSum &acc) {
   float xf[4], wf[4], vf[4], uf[4], g[4];
   Storage<float>::unpack(q.x, xf);
   bool slow = false;
@@ -220,7 +235,7 @@ __device__ __forceinline__ bool loss_vector_fast(const LossVec &q, size_t i, flo
   float part = 0.0f;
 #pragma unroll
   for (int e = 0; e < 4; ++e) part += loss_element<false>(xf[e], wf[e], vf[e], uf[e], lo, hi, tab, g[e]);
-  acc += (double)part;
+  acc.add(part);
   st_stream(reinterpret_cast<uint4 *>(gx) + i, Storage<float>::pack(g));
   return true;
 }
@@ -259,8 +274,9 @@ static __device__ __noinline__ double loss_elements(const float *x, const float 
 }
 
 // Persistent grid over 16-byte vectors of x, w, v, u with a ring of two
-// vector quadruples in flight per thread (as in k_map); per-thread FP64
-// partial sums, reduced per block and added to *loss with one atomic.
+// vector quadruples in flight per thread (as in k_map); per-thread float
+// TwoSum partial sums, reduced in FP64 per block and added to *loss with one
+// atomic.
 __global__ void __launch_bounds__(256) k_loss(const float *__restrict__ x, const float *__restrict__ w,
                                               const float *__restrict__ v, const float *__restrict__ u, size_t n,
                                               float lo, float hi, double *loss, float *__restrict__ gx) {
@@ -269,6 +285,7 @@ __global__ void __launch_bounds__(256) k_loss(const float *__restrict__ x, const
   __shared__ double s_sum[8];
   if (threadIdx.x < 8) s_tab[threadIdx.x] = c_tab_f32[threadIdx.x];
   __syncthreads();
+  FSum fast;
   double acc = 0.0;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   const bool aligned = (((uintptr_t)x | (uintptr_t)w | (uintptr_t)v | (uintptr_t)u | (uintptr_t)gx) & 15u) == 0;
@@ -290,7 +307,7 @@ __global__ void __launch_bounds__(256) k_loss(const float *__restrict__ x, const
         const LossVec cur = buf[d];
         const size_t jn = ii + (size_t)D * stride;
         if (jn < nvec) buf[d] = load_loss_vec(x, w, v, u, jn);
-        if (!loss_vector_fast(cur, ii, lo, hi, s_tab, gx, acc)) {
+        if (!loss_vector_fast(cur, ii, lo, hi, s_tab, gx, fast)) {
           resume = ii + 1;
           goto full;
         }
@@ -302,6 +319,7 @@ full:
   acc += loss_resume_full(x, w, v, u, resume - 1, nvec, stride, lo, hi, s_tab, gx);
 rest:
   if (nvec * 4 < n) acc += loss_elements(x, w, v, u, nvec * 4 + first, n, stride, lo, hi, s_tab, gx);
+  acc += fast.value();
   // block sum: warp shuffles, then one double atomic per block
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = acc;

@@ -3,17 +3,17 @@
 #pragma once
 #include <stdint.h>
 
-/* pi/2 = PIO2_F1 + PIO2_F2 + PIO2_F3 (+ ~2^-60): 12 + 24 + 24 bits */
-#define PTRIG_PIO2_F1 0x1.9200000000000p+0f
-#define PTRIG_PIO2_F2 0x1.fb54440000000p-12f
-#define PTRIG_PIO2_F3 0x1.68c2340000000p-39f
+/* pi/2 = PIO2_F1 + PIO2_F2 + PIO2_F3 (+ < 2^-70): three positive 24-bit floats, used with FMA */
+#define PTRIG_PIO2_F1 0x1.921fb40000000p+0f
+#define PTRIG_PIO2_F2 0x1.4442d00000000p-24f
+#define PTRIG_PIO2_F3 0x1.84698a0000000p-48f
 #define PTRIG_2_OVER_PI_F 0x1.45f3060000000p-1f
 #define PTRIG_12_OVER_PI_F 0x1.e8ec8a0000000p+1f
 #define PTRIG_PIO2_F 0x1.921fb60000000p+0f
 /* 1.5 * 2^23: adding it rounds a float to an integer held in the low mantissa bits */
 #define PTRIG_RINT_MAGIC_F 0x1.8000000000000p+23f
-/* largest float <= 2^10 pi: FP32 reduction bound (FP64 or Payne-Hanek above) */
-#define PTRIG_FAST_LIMIT_F 0x1.921fb40000000p+11f
+/* FP32 reduction bound 2^20 (FP64 Cody-Waite or Payne-Hanek above) */
+#define PTRIG_FAST_LIMIT_F 0x1.0000000000000p+20f
 
 /* pi/2 = PIO2_D1 + PIO2_D2 + PIO2_D3 (+ ~2^-127): 21 + 53 + 53 bits */
 #define PTRIG_PIO2_D1 0x1.921fb00000000p+0

@@ -5,7 +5,7 @@
 //   1. reduction  x = j pi/2 + r with |r| <~ pi/4 (Sec. 3 reduces to [0, pi/2]
 //      with a sign; here the nearest multiple of pi/2 is taken and the paper's
 //      angle is u = t for even j, u = pi/2 - t for odd j, t = |r|):
-//        |x| <= 2^10 pi : FP32 Cody-Waite, 12+24+24-bit split of pi/2
+//        |x| <= 2^20    : FP32 Cody-Waite with FMA, 24+24+24-bit split of pi/2
 //        |x| <  2^31    : FP64 Cody-Waite, 21+53+53-bit split
 //        otherwise      : Payne-Hanek, exact integer product with 2/pi
 //   2. segment  kq = floor(t 12/pi) in 0..3; segment k = kq (even j) or
@@ -73,9 +73,16 @@ struct RedF {
   uint32_t jb;  // low bits hold j (two's complement); only j & 3 is used
 };
 
-// FP32 Cody-Waite for |x| <= 2^10 pi.  j = rint(x 2/pi) comes out of the
-// 1.5*2^23 rounding trick; j * PIO2_F1 is exact (12-bit head, |j| <= 2048) and
-// x - j PIO2_F1 is exact as well, so r is accurate to about one ulp of r.
+// FP32 Cody-Waite for |x| <= 2^20.  j = rint(x 2/pi) comes out of the
+// 1.5*2^23 rounding trick (possibly one off the nearest multiple when x 2/pi
+// is within 0.04 of a half-integer, so |r| <= 0.54 pi/2 < pi/3, which the
+// table's segments still cover).  PIO2_F1 (pi/2 truncated to 24 bits) has
+// ulp 2^-23, so the first FMA, x - j PIO2_F1, has no bit below 2^-24 and
+// |.| < 1: it is exact.  The two later FMAs round once each and PIO2_F1..F3
+// leave a tail below 2^-70, so |r - (x - j pi/2)| <= 2^-23 |r| + 2^-49.65; no
+// float in (0.5, 2^20] lies within 2^-27.8 of a multiple of pi/2, so r keeps
+// a relative error below 2^-21.2.  The three pieces are positive: for x = -0
+// (j = +0) every product -j PIO2_Fk is -0 and r stays -0.
 __device__ __forceinline__ RedF reduce_fast(float x) {
   const float y = __fmaf_rn(x, PTRIG_2_OVER_PI_F, PTRIG_RINT_MAGIC_F);
   const float jf = __fsub_rn(y, PTRIG_RINT_MAGIC_F);
@@ -192,7 +199,7 @@ __device__ __forceinline__ double reduce_d(double x, uint32_t *jb) {
   return reduce_payne_hanek(x, jb);
 }
 
-// Side path for FP32 inputs with |x| > 2^10 pi, infinities and NaN.
+// Side path for FP32 inputs with |x| > 2^20, infinities and NaN.
 static __device__ __noinline__ RedF reduce_slow_f32(float x) {
   if (!isfinite(x)) return {__int_as_float(0x7fffffff), 0u};
   uint32_t jb;
@@ -283,7 +290,7 @@ __device__ __forceinline__ void proposed_pair_mag(float2 x, const float4 *tab, f
   }
 }
 
-// FULL = false: the caller guarantees |x| <= 2^10 pi (FP32 reduction only).
+// FULL = false: the caller guarantees |x| <= 2^20 (FP32 reduction only).
 template <bool FULL>
 __device__ __forceinline__ RedF reduce_sel(float x) {
   return FULL ? reduce_f32(x) : reduce_fast(x);

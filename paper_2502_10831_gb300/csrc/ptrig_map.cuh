@@ -70,7 +70,7 @@ __device__ __forceinline__ bool map_vector_fast(uint4 v, size_t i, T *y0, T *y1,
 
 // Vectors i, i + stride, ... < nvec with the full reduction (FP32 Cody-Waite,
 // FP64 Cody-Waite or Payne-Hanek per element).  Out of line and reached only
-// after a thread met an angle beyond 2^10 pi, so the pipelined loop carries no
+// after a thread met an angle beyond 2^20, so the pipelined loop carries no
 // call and no FP64 / Payne-Hanek register state.
 template <typename T, class F>
 static __device__ __noinline__ void map_resume_full(const T *__restrict__ x, T *__restrict__ y0,
@@ -96,16 +96,9 @@ static __device__ __noinline__ void map_resume_full(const T *__restrict__ x, T *
 //     a grid of a few blocks per SM walks the whole array.
 //   one-shot   (PERSIST = false): base = b*B*D + t, step = B, end = base + D*B;
 //     each block streams one contiguous chunk of D*B vectors and retires.
-// Single-output functions on 16-bit storage are instruction-bound: their
-// registers are capped at 64 (two 512-thread blocks per SM) for more resident
-// warps.  FP32 is memory-bound and sincos would spill, so both keep the
-// compiler's choice.
-template <typename T, class F>
-constexpr int map_min_blocks() { return (sizeof(T) == 2 && F::NOUT == 1) ? 2 : 1; }
-
 template <typename T, class F, int D, bool PERSIST>
-__global__ void __launch_bounds__(512, map_min_blocks<T, F>()) k_map(const T *__restrict__ x, T *__restrict__ y0, T *__restrict__ y1,
-                                             size_t n) {
+__device__ __forceinline__ void map_stream(const T *__restrict__ x, T *__restrict__ y0, T *__restrict__ y1,
+                                           size_t n) {
   __shared__ float4 s_tab[8];
   if (threadIdx.x < 8) s_tab[threadIdx.x] = c_tab_f32[threadIdx.x];
   __syncthreads();
@@ -162,6 +155,34 @@ full:
   map_resume_full<T, F>(x, y0, y1, resume - 1, end, step, s_tab);
 }
 
+template <typename T, class F, int D, bool PERSIST>
+__global__ void __launch_bounds__(512) k_map(const T *__restrict__ x, T *__restrict__ y0, T *__restrict__ y1,
+                                             size_t n) {
+  map_stream<T, F, D, PERSIST>(x, y0, y1, n);
+}
+
+// Single-output functions on 16-bit storage are instruction-bound: this
+// instance caps their registers at 64 (two 512-thread blocks per SM) for more
+// resident warps.  FP32 is memory-bound and sincos would spill, so both keep
+// k_map; on GB300 even a minimum of one block per SM in the launch bounds
+// slowed the FP32 kernels by 5-10% at the same register count.
+template <typename T, class F, int D, bool PERSIST>
+__global__ void __launch_bounds__(512, 2) k_map_capped(const T *__restrict__ x, T *__restrict__ y0,
+                                                       T *__restrict__ y1, size_t n) {
+  map_stream<T, F, D, PERSIST>(x, y0, y1, n);
+}
+
+template <typename T, class F>
+constexpr bool map_capped() { return sizeof(T) == 2 && F::NOUT == 1; }
+
+template <typename T, class F, int D, bool PERSIST>
+void launch_k_map(unsigned grid, int block, cudaStream_t s, const T *x, T *y0, T *y1, size_t n) {
+  if constexpr (map_capped<T, F>())
+    k_map_capped<T, F, D, PERSIST><<<grid, block, 0, s>>>(x, y0, y1, n);
+  else
+    k_map<T, F, D, PERSIST><<<grid, block, 0, s>>>(x, y0, y1, n);
+}
+
 // Any alignment: one element per thread per iteration.
 template <typename T, class F>
 __global__ void __launch_bounds__(512) k_map_scalar(const T *__restrict__ x, T *__restrict__ y0,
@@ -197,10 +218,10 @@ ptrig_status launch_map_d(const LaunchCfg &c, int sms, const T *x, T *y0, T *y1,
     const size_t cap = (size_t)sms * (size_t)c.blocks_per_sm;
     if (g > cap) g = cap;
     if (g < 1) g = 1;
-    k_map<T, F, D, true><<<(unsigned)g, c.block, 0, s>>>(x, y0, y1, n);
+    launch_k_map<T, F, D, true>((unsigned)g, c.block, s, x, y0, y1, n);
   } else {  // one-shot: one contiguous chunk of D * block vectors per block
     const size_t g = grid_for(nvec, (size_t)c.block * D, LaunchCfg{c.block, D, 0}, sms);
-    k_map<T, F, D, false><<<(unsigned)g, c.block, 0, s>>>(x, y0, y1, n);
+    launch_k_map<T, F, D, false>((unsigned)g, c.block, s, x, y0, y1, n);
   }
   return finish_launch();
 }

@@ -192,8 +192,8 @@ def edge_values() -> np.ndarray:
     for j in (1, 3, 5, 7, 101, 199, 2047, 2049, 65535):
         c = f(j * PI / 2.0)
         vals += [c, -c, np.nextafter(c, f(np.inf)), np.nextafter(c, f(-np.inf))]
-    b = f(1024.0 * PI)
-    vals += [b, -b, np.nextafter(b, f(0.0)), np.nextafter(b, f(np.inf))]
+    for b in (f(1024.0 * PI), f(2.0 ** 20), f(2.0 ** 31)):
+        vals += [b, -b, np.nextafter(b, f(0.0)), np.nextafter(b, f(np.inf))]
     vals += [1e5, -1e5, 1e6, 3.0e9, -6.7e9, 1e10, 2.0 ** 40, 1e20, -1e30, 3.4e38, -3.4e38]
     vals += [np.inf, -np.inf, np.nan]
     return np.array(vals, dtype=np.float32)

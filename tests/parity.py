@@ -71,3 +71,34 @@ def check_values(oracle, func: str, xd: np.ndarray, y: np.ndarray, ref: np.ndarr
         f"tan: |delta| {err[worst]:.3e} vs ref {rf[keep][worst]:.3e} at x={xd[finite][keep][worst]!r}")
     nz = rf[keep] != 0
     return float((err[nz] / np.abs(rf[keep][nz])).max()) if nz.any() else 0.0
+
+
+def closest_to_half_pi_multiples(oracle, e_lo: int = -1, e_hi: int = 20, k: int = 6) -> np.ndarray:
+    """The k positive floats of each binade [2^e, 2^(e+1)), e_lo <= e <= e_hi,
+    that lie closest to a nonzero multiple of pi/2, and their negatives: the
+    inputs whose reduced angle cancels most.  Exhaustive over each binade; the
+    distance is computed in double with pi/2 split into four 26-bit pieces
+    (j times a piece is exact for |j| < 2^27)."""
+    half_pi = oracle.pi_fixed(200) // 2  # pi/2 * 2^200, truncated
+    pieces = []
+    rem = half_pi
+    for _ in range(4):
+        e = rem.bit_length() - 26
+        p = (rem >> e) << e
+        pieces.append(math.ldexp(p >> e, e - 200))
+        rem -= p
+    c = 2.0 / math.pi
+    out = []
+    for e in range(e_lo, e_hi + 1):
+        lo = int(np.float32(2.0 ** e).view(np.uint32))
+        bits = np.arange(lo, lo + (1 << 23), dtype=np.uint32)
+        x = bits.view(np.float32).astype(np.float64)
+        j = np.rint(x * c)
+        r = x - j * pieces[0]
+        for p in pieces[1:]:
+            r = r - j * p
+        a = np.where(j == 0, np.inf, np.abs(r))
+        idx = np.argpartition(a, k)[:k]
+        out.append(x[idx])
+    v = np.concatenate(out).astype(np.float32)
+    return np.concatenate([v, -v])

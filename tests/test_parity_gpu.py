@@ -101,16 +101,45 @@ def test_edge_values(B, oracle):
 
 @pytest.mark.parametrize("func", ("sin", "tan"))
 def test_large_arguments(B, oracle, func):
-    """|x| log-uniform in [1, 1e5] (FP64 Cody-Waite side path above 2^10 pi)
-    plus Payne-Hanek magnitudes up to the largest float."""
+    """|x| log-uniform in [1, 1e5] (FP32 reduction), in (2^20, 2^31) (FP64
+    Cody-Waite side path) and up to the largest float (Payne-Hanek)."""
     big = workloads.large(1 << 20)
     r = np.random.default_rng(4)
+    mid = (2.0 ** r.uniform(20.0, 31.0, 1 << 16) * r.choice([-1, 1], 1 << 16)).astype(np.float32)
     huge = (10.0 ** r.uniform(9.5, 38.5, 4096) * r.choice([-1, 1], 4096)).astype(np.float32)
-    x = np.concatenate([big, huge[np.isfinite(huge)]])
+    x = np.concatenate([big, mid, huge[np.isfinite(huge)]])
     xd = x.astype(np.float64)
     y = _run(B, func, x)
     ref, _ = P.reference_with_gpu_segments(oracle, func, xd, _segments(B, x))
     P.check_values(oracle, func, xd, y, ref)
+
+
+@pytest.fixture(scope="module")
+def worst_reduction():
+    return P.closest_to_half_pi_multiples(oracle_module(), -1, 20, 6)
+
+
+def oracle_module():
+    from oracle import ptrig_oracle as O
+    return O
+
+
+@pytest.mark.parametrize("func", FUNCS)
+def test_reduction_worst_cases(B, oracle, worst_reduction, func):
+    """The floats of every binade up to 2^21 that lie closest to a multiple of
+    pi/2 (the largest cancellation in the FP32 reduction): the usual bounds,
+    and a relative bound of 2^-18 wherever the result is small (sin at even,
+    cos at odd multiples) or for tan everywhere (zero or pole)."""
+    x = worst_reduction
+    xd = x.astype(np.float64)
+    y = _run(B, func, x)
+    ref, _ = P.reference_with_gpu_segments(oracle, func, xd, _segments(B, x))
+    P.check_values(oracle, func, xd, y, ref)
+    small = np.ones(x.shape, bool) if func == "tan" else np.abs(ref) < 1e-2
+    assert small.sum() >= 40
+    err = np.abs(y[small].astype(np.float64) - ref[small])
+    bound = 2.0 ** -18 * np.abs(ref[small]) + 2.0 ** -149
+    assert np.all(err <= bound), (func, xd[small][np.argmax(err / bound)], float((err / bound).max()))
 
 
 # ------------------------------------------------- sizes, alignment, in place

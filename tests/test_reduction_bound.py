@@ -1,0 +1,53 @@
+"""The FP32 reduction's error bound, checked on the CPU from its constants.
+
+The kernels reduce |x| <= PTRIG_FAST_LIMIT_F with three FMAs against
+pi/2 = P1 + P2 + P3 + tail.  The bound |r - (x - j pi/2)| <= 2^-23 |r| + 2^-49.65
+rests on: P1 having ulp 2^-23 (first FMA exact), positive pieces (x = -0 keeps
+its sign), |j| < 2^20, a tail below 2^-70, and no float up to the limit lying
+within 2^-27.8 of a nonzero multiple of pi/2 (relative error of r below 2^-21.2).
+"""
+import math
+import os
+import re
+from fractions import Fraction
+
+import numpy as np
+
+import parity as P
+
+HDR = os.path.join(os.path.dirname(__file__), "..", "paper_2502_10831_gb300", "csrc", "ptrig_constants.h")
+
+
+def _const(name):
+    m = re.search(rf"#define {name} (\S+)f\n", open(HDR).read())
+    return float.fromhex(m.group(1))
+
+
+def _half_pi(oracle):
+    return Fraction(oracle.pi_fixed(400), 1 << 401)
+
+
+def test_pieces_positive_and_sum_to_half_pi(oracle):
+    p = [_const(f"PTRIG_PIO2_F{k}") for k in (1, 2, 3)]
+    assert all(v > 0 for v in p)
+    for v in p:
+        assert np.float32(v) == v
+    assert math.frexp(p[0])[1] == 1  # P1 in [1, 2): ulp 2^-23
+    tail = _half_pi(oracle) - sum(Fraction(v) for v in p)
+    assert abs(tail) < Fraction(1, 2 ** 70)
+
+
+def test_limit_and_quotient_range():
+    lim = _const("PTRIG_FAST_LIMIT_F")
+    assert lim == 2.0 ** 20
+    jmax = lim * _const("PTRIG_2_OVER_PI_F") + 1
+    assert jmax < 2 ** 20 and jmax < 2 ** 22  # |j| fits the 1.5*2^23 rounding trick
+
+
+def test_no_float_closer_than_bound_to_half_pi_multiple(oracle):
+    worst = P.closest_to_half_pi_multiples(oracle, -1, 19, 1)
+    u, _, _, _, _ = oracle.reduce(worst.astype(np.float64))
+    d = np.minimum(u, np.pi / 2 - u)
+    assert np.log2(d.min()) > -27.9
+    # relative error of r at the closest float stays below 2^-21.2
+    assert 2.0 ** -23 + 2.0 ** -49.65 / d.min() < 2.0 ** -21.2
