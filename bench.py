@@ -121,7 +121,7 @@ def oracle_rate(x_host, seconds_budget: float = 12.0, threads: int | None = None
 
     O.lib()
     threads = threads or os.cpu_count() or 1
-    m = min(x_host.size, 1 << 22)
+    m = min(x_host.size, 1 << 23)
     xd = x_host[:m].astype(np.float64)
     parts = np.array_split(xd, threads)
 
@@ -142,6 +142,32 @@ def oracle_rate(x_host, seconds_budget: float = 12.0, threads: int | None = None
     return {"value": evals / dt / 1e9, "unit": "Gelem/s", "cores": threads, "kind": "oracle",
             "sample": f"first {m} angles of the workload x 7 functions (sincos counted once), "
                       f"{threads} threads, {dt:.2f} s wall"}
+
+
+def cpu_simd_rate(x_host):
+    """The CPU SIMD baseline (cpu_simd/, vectorised across angles, one thread
+    per online core) over the whole workload: each proposed function of the
+    step once, outputs pre-touched, wall-clock timed."""
+    import numpy as np
+
+    from cpu_simd import ptrig_cpu as C
+
+    threads = C.default_threads()
+    y0 = np.zeros_like(x_host)
+    y1 = np.zeros_like(x_host)
+    C.evaluate("sincos", x_host[: 1 << 20], threads, out=(y0[: 1 << 20], y1[: 1 << 20]))
+    per = {}
+    total_t = 0.0
+    for f in ("sin", "cos", "tan", "sincos"):
+        t0 = time.perf_counter()
+        C.evaluate(f, x_host, threads, out=(y0, y1))
+        dt = time.perf_counter() - t0
+        total_t += dt
+        per[f] = {"s": round(dt, 4), "gelem_s": round(x_host.size / dt / 1e9, 3)}
+    return {"value": round(4 * x_host.size / total_t / 1e9, 3), "unit": "Gelem/s", "cores": threads,
+            "kind": "cpu_simd", "per_function": per,
+            "sample": f"all {x_host.size} angles of the workload x the 4 proposed functions (sin, cos, tan, "
+                      f"sincos; sincos counted once), FP32, {threads} threads"}
 
 
 # ---------------------------------------------------------------- reference
@@ -515,6 +541,7 @@ def extras(args, B, W, x, x_host, n, stream, peak, kernels):
     torch.cuda.empty_cache()
     out["e2e"] = e2e(B, x_host, n, x.device, stream)
     out["cpu_baseline"] = oracle_rate(x_host)
+    out["cpu_simd"] = cpu_simd_rate(x_host)
     return out
 
 

@@ -10,6 +10,7 @@
 """
 from __future__ import annotations
 
+import functools
 import math
 
 import numpy as np
@@ -73,12 +74,14 @@ def check_values(oracle, func: str, xd: np.ndarray, y: np.ndarray, ref: np.ndarr
     return float((err[nz] / np.abs(rf[keep][nz])).max()) if nz.any() else 0.0
 
 
+@functools.lru_cache(maxsize=4)
 def closest_to_half_pi_multiples(oracle, e_lo: int = -1, e_hi: int = 20, k: int = 6) -> np.ndarray:
     """The k positive floats of each binade [2^e, 2^(e+1)), e_lo <= e <= e_hi,
     that lie closest to a nonzero multiple of pi/2, and their negatives: the
     inputs whose reduced angle cancels most.  Exhaustive over each binade; the
     distance is computed in double with pi/2 split into four 26-bit pieces
-    (j times a piece is exact for |j| < 2^27)."""
+    (j times a piece is exact for |j| < 2^27).  Cached per arguments: treat
+    the returned array as read-only."""
     half_pi = oracle.pi_fixed(200) // 2  # pi/2 * 2^200, truncated
     pieces = []
     rem = half_pi

@@ -111,11 +111,23 @@ def test_batch_plan_rejects_bad_descriptors(lib):
 
 
 def test_product_path_does_not_reference_the_oracle():
-    """The package never imports, loads or runs anything under oracle/."""
+    """The package never imports, loads or runs anything under oracle/, nor
+    the CPU SIMD baseline under cpu_simd/ (no CPU fallback)."""
     pkg = os.path.join(ROOT, "paper_2502_10831_gb300")
     for dirpath, _, files in os.walk(pkg):
         for f in files:
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 src = open(os.path.join(dirpath, f)).read()
-                for pat in (r"\bimport\s+oracle", r"\bfrom\s+oracle\b", r"ptrig_oracle", r"ptro_"):
+                for pat in (r"\bimport\s+oracle", r"\bfrom\s+oracle\b", r"ptrig_oracle", r"ptro_",
+                            r"cpu_simd", r"ptrig_cpu"):
                     assert not re.search(pat, src), (f, pat)
+
+
+def test_cpu_baseline_does_not_reference_the_oracle():
+    """cpu_simd/ is a third implementation: it shares nothing with oracle/."""
+    d = os.path.join(ROOT, "cpu_simd")
+    for f in os.listdir(d):
+        if f.endswith((".py", ".c", ".h")):
+            src = open(os.path.join(d, f)).read()
+            for pat in (r"\bimport\s+oracle", r"\bfrom\s+oracle\b", r"ptrig_oracle", r"ptro_"):
+                assert not re.search(pat, src), (f, pat)

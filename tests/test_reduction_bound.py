@@ -45,7 +45,7 @@ def test_limit_and_quotient_range():
 
 
 def test_no_float_closer_than_bound_to_half_pi_multiple(oracle):
-    worst = P.closest_to_half_pi_multiples(oracle, -1, 19, 1)
+    worst = P.closest_to_half_pi_multiples(oracle, -1, 20, 6)
     u, _, _, _, _ = oracle.reduce(worst.astype(np.float64))
     d = np.minimum(u, np.pi / 2 - u)
     assert np.log2(d.min()) > -27.9
