@@ -329,7 +329,14 @@ def workload_autograd(B, W, torch, dev, rank, log2n):
         B.ptrig_sincostan_loss_f32(x.detach(), w, v, u, -50.0, 50.0, loss_buf, gx_buf, n,
                                    torch.cuda.current_stream().cuda_stream)
 
-    return ks, meta, {"fused": fused, "fused_kernel": fused_kernel, "n": n}
+    gy = torch.randn(x.shape, device=dev)
+
+    def bwd_kernel(f):
+        return lambda: getattr(B, f"ptrig_{f}_bwd_f32")(x.detach(), gy, gx_buf, n,
+                                                        torch.cuda.current_stream().cuda_stream)
+
+    return ks, meta, {"fused": fused, "fused_kernel": fused_kernel, "n": n,
+                      "bwd": {f: bwd_kernel(f) for f in ("sin", "cos", "tan")}}
 
 
 WORKLOADS = {"bandwidth": workload_bandwidth, "half": workload_half, "large": workload_large,
@@ -457,6 +464,12 @@ def main():
                                      "their derivatives from one reduction; reads x, w, v, u, writes dL/dx, "
                                      "20 B/angle), then backward scales dL/dx by the incoming gradient (a torch "
                                      "multiply, 8 B/angle); kernel_* times the library call alone"}
+        bk = {}
+        for f, call in state["bwd"].items():
+            bms = _time_call(call, 20, stream)
+            bk[f"{f}_bwd_f32"] = {"ms": round(bms, 4), "gelem_s": round(nn / bms / 1e6, 2),
+                                  "hbm_frac": round(12 * nn / bms / 1e6 / peak, 4)}
+        line["backward_kernels"] = bk
     if args.workload == "large" and rank == 0:
         line["side_paths"] = side_paths(B, torch, dev, stream, peak)
     if args.workload == "bandwidth" and not args.no_extras and rank == 0:
