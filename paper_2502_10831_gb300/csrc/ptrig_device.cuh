@@ -240,9 +240,18 @@ __device__ __forceinline__ float xor_sign(float v, uint32_t sbit) {
 
 // ------------------------------------------------------ proposed, FP32 math
 
+// kq = floor(t 12/pi) for 0 <= t < pi/3, as t 12/pi - 1/2 rounded to the
+// nearest integer by the 1.5*2^23 trick (one FFMA and one FADD on the FMA
+// pipe instead of a conversion on the XU pipe).  It differs from the floor of
+// the rounded product only where t 12/pi lies within an FP32 rounding of an
+// integer, i.e. at a node k pi/12, where both adjacent segments are valid.
+__device__ __forceinline__ uint32_t segment_kq(float t) {
+  const float z = __fmaf_rn(t, PTRIG_12_OVER_PI_F, -0.5f);
+  return __float_as_uint(__fadd_rn(z, PTRIG_RINT_MAGIC_F)) & 3u;
+}
+
 __device__ __forceinline__ uint32_t table_index(float t, uint32_t jb) {
-  const int kq = __float2int_rd(t * PTRIG_12_OVER_PI_F);
-  return ((jb & 1u) << 2) | ((uint32_t)kq & 3u);
+  return ((jb & 1u) << 2) | segment_kq(t);
 }
 
 // Pair form for 16-bit storage: magnitudes m0 (and m1 for sincos), all >= 0,
@@ -258,9 +267,11 @@ __device__ __forceinline__ void proposed_pair_mag(float2 x, const float4 *tab, f
                                                   uint32_t &s0, uint32_t &s1) {
   const RedF2 red = reduce_fast2(x);
   const float2 t = make_float2(fabsf(red.r.x), fabsf(red.r.y));
-  const float2 v = __fmul2_rn(t, make_float2(PTRIG_12_OVER_PI_F, PTRIG_12_OVER_PI_F));
-  const uint32_t i0 = ((red.jb0 & 1u) << 2) | ((uint32_t)__float2int_rd(v.x) & 3u);
-  const uint32_t i1 = ((red.jb1 & 1u) << 2) | ((uint32_t)__float2int_rd(v.y) & 3u);
+  // segment_kq() for both lanes with packed FFMA2 / FADD2
+  const float2 z = __ffma2_rn(t, make_float2(PTRIG_12_OVER_PI_F, PTRIG_12_OVER_PI_F), make_float2(-0.5f, -0.5f));
+  const float2 v = __fadd2_rn(z, make_float2(PTRIG_RINT_MAGIC_F, PTRIG_RINT_MAGIC_F));
+  const uint32_t i0 = ((red.jb0 & 1u) << 2) | (__float_as_uint(v.x) & 3u);
+  const uint32_t i1 = ((red.jb1 & 1u) << 2) | (__float_as_uint(v.y) & 3u);
   const float4 c0 = tab[i0];
   const float4 c1 = tab[i1];
   const float2 N = make_float2(__fmaf_rn(c0.x, t.x, c0.y), __fmaf_rn(c1.x, t.y, c1.y));

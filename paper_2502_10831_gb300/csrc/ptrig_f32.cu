@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(256) k_segment(const float *__restrict__ x, ui
     }
     const RedF red = reduce_f32(xv);
     const float t = fabsf(red.r);
-    const uint32_t kq = (uint32_t)__float2int_rd(t * PTRIG_12_OVER_PI_F) & 3u;
+    const uint32_t kq = segment_kq(t);
     const uint32_t seg = (red.jb & 1u) ? 5u - kq : kq;
     const uint32_t q = signbit(xv) ? ((0u - red.jb) - (red.r > 0.0f ? 1u : 0u)) & 3u
                                    : (red.jb - (red.r < 0.0f ? 1u : 0u)) & 3u;

@@ -310,6 +310,67 @@ def test_half_parity(B, oracle, func, dt):
             assert rel.max() <= tol, (dt, rel.max())
 
 
+# 16-bit storage: significand bits, smallest normal exponent, largest finite
+_HALF_FMT = {"f16": (11, -14, 65504.0), "bf16": (8, -126, float(np.float32(3.3895313892515355e38)))}
+# Relative bound on the FP32 value before the final rounding: the reduction's
+# 2^-21.2 times a conditioning of at most 2 (no formula row cancels: N or D is
+# exactly proportional to t where it vanishes), plus a few FP32 roundings and
+# the hardware rsqrt / rcp approximations.
+_HALF_EPS = 2.0 ** -18
+
+
+def _round_neighbours(ref, fmt):
+    """For |ref|: the two storage-grid values around it (lo <= |ref| <= hi),
+    the round-to-nearest-even choice, and whether |ref| lies within
+    _HALF_EPS relative of the midpoint between lo and hi."""
+    p, emin, maxf = _HALF_FMT[fmt]
+    a = np.abs(ref)
+    _, ex = np.frexp(np.where(a > 0, a, 1.0))
+    e = np.maximum(ex - 1, emin)
+    ulp = np.ldexp(1.0, e - (p - 1))
+    lo = np.floor(a / ulp) * ulp
+    hi = lo + ulp
+    mid = lo + ulp / 2
+    even_lo = (np.floor(a / ulp) % 2) == 0
+    rn = np.where(a < mid, lo, np.where(a > mid, hi, np.where(even_lo, lo, hi)))
+    rn = np.where(rn > maxf, np.inf, rn)
+    hi = np.where(hi > maxf, np.inf, hi)
+    near = np.abs(a - mid) <= _HALF_EPS * a
+    return lo, hi, rn, near
+
+
+@pytest.mark.parametrize("dt", ["f16", "bf16"])
+@pytest.mark.parametrize("func", ("sin", "cos", "tan"))
+def test_half_exhaustive_correctly_rounded(B, oracle, func, dt):
+    """Every one of the 65536 bit patterns: NaN for NaN / inf inputs, and
+    otherwise the oracle value rounded to nearest in the storage type -- or,
+    only where the oracle value lies within 2^-18 relative of a rounding
+    midpoint, the other neighbour.  Signs must agree."""
+    bits = np.arange(1 << 16, dtype=np.uint32).astype(np.uint16)
+    with np.errstate(invalid="ignore"):  # signalling-NaN patterns
+        xd = (bits.view(np.float16).astype(np.float64) if dt == "f16"
+              else workloads.bf16_bits_to_f32(bits).astype(np.float64))
+    xt = _dev(bits.view(np.int16))
+    y = torch.empty_like(xt)
+    getattr(B, f"ptrig_{func}_{dt}")(xt, y)
+    torch.cuda.synchronize()
+    raw = y.cpu().numpy().view(np.uint16)
+    with np.errstate(invalid="ignore"):
+        got = (raw.view(np.float16).astype(np.float64) if dt == "f16"
+               else workloads.bf16_bits_to_f32(raw).astype(np.float64))
+    fin = np.isfinite(xd)
+    assert np.all(np.isnan(got[~fin]))
+    xf, gf = xd[fin], got[fin]
+    ref, _ = P.reference_with_gpu_segments(oracle, func, xf, _segments(B, xf.astype(np.float32)))
+    lo, hi, rn, near = _round_neighbours(ref, dt)
+    ga = np.abs(gf)
+    ok = (ga == rn) | (near & ((ga == lo) | (ga == hi)))
+    nz = (ref != 0) & (gf != 0)
+    ok &= ~nz | (np.signbit(gf) == np.signbit(ref))
+    bad = np.flatnonzero(~ok)
+    assert bad.size == 0, (dt, func, bad.size, xf[bad[:4]], gf[bad[:4]], ref[bad[:4]])
+
+
 @pytest.mark.parametrize("dt", ["f16", "bf16"])
 def test_half_vector_and_scalar_paths_agree(B, dt):
     """Aligned arrays take the 16-byte vector path (packed FP32 pairs);
