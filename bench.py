@@ -271,8 +271,8 @@ def workload_large(B, W, torch, dev, rank, log2n):
     return ks, meta, {"n": n}
 
 
-def workload_batch(B, W, torch, dev, rank, log2n):
-    lengths, sel = W.batch_spec(4096, seed=R.shard_seed(W.SEED, rank))
+def workload_batch(B, W, torch, dev, rank, log2n, arrays=4096, config=None):
+    lengths, sel = W.batch_spec(arrays, seed=R.shard_seed(W.SEED, rank))
     total = int(lengths.sum())
     padded = int(sum((int(n) + 63) // 64 * 64 for n in lengths))
     xs = torch.empty(padded, dtype=torch.float32, device=dev)
@@ -286,12 +286,17 @@ def workload_batch(B, W, torch, dev, rank, log2n):
         nbytes += (12 if f == 3 else 8) * n
         off += (n + 63) // 64 * 64  # each array starts on a 256-byte boundary, as separate allocations would
     plan = B.BatchPlan(descs, B.BATCH_GRAPH)
-    tuned = plan.autotune(reps=3)
+    if config:
+        plan.set_config(*config)
+        tuned = {"block": config[0], "items_per_thread": config[1], "fixed": True}
+    else:
+        tuned = plan.autotune(reps=3)
     s = torch.cuda.current_stream().cuda_stream
-    ks = [Kernel("batch_graph", nbytes, total, lambda: plan.run(s))]
-    meta = {"metric": "Gelem/s, ragged batch of 4096 fp32 arrays (per-array sin/cos/tan/sincos) in one persistent "
-                      "launch captured in a CUDA graph",
-            "dtype": "f32", "workload": f"batching: 4096 arrays, lengths floor(exp U[ln 100, ln 1e6]) "
+    nops = len(set(int(f) for f in sel))
+    ks = [Kernel("batch_graph", nbytes, total, lambda: plan.run(s), launches=nops)]
+    meta = {"metric": f"Gelem/s, ragged batch of {arrays} fp32 arrays (per-array sin/cos/tan/sincos), one kernel "
+                      "per function over a tile table, the launches captured in one CUDA graph",
+            "dtype": "f32", "workload": f"batching: {arrays} arrays, lengths floor(exp U[ln 100, ln 1e6]) "
                                         f"(total {total}), values U[-8pi, 8pi], selectors uniform",
             "n_per_gpu": total, "l2": "inputs larger than L2, no flush", "autotuned": tuned}
     return ks, meta, {"plan": plan, "descs": descs}
@@ -351,6 +356,10 @@ def main():
     ap.add_argument("--impl", default="ptrig", choices=["ptrig", "reference"])
     ap.add_argument("--workload", default="bandwidth", choices=sorted(WORKLOADS))
     ap.add_argument("--log2n", type=int, default=28)
+    ap.add_argument("--batch-arrays", type=int, default=4096,
+                    help="arrays in the batch workload (4096 is the configured batch; fewer for profiling)")
+    ap.add_argument("--batch-config", default=None,
+                    help="BLOCK,ITEMS: fixed batch tile shape instead of the autotuner (for profiling)")
     ap.add_argument("--no-extras", action="store_true", help="skip half/cuda-math/e2e/cpu legs")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -374,7 +383,12 @@ def main():
     Bld.build()
     B.lib()
     dev = torch.device("cuda", local)
-    kernels_list, meta, state = WORKLOADS[args.workload](B, W, torch, dev, rank, args.log2n)
+    wl_kw = {}
+    if args.workload == "batch":
+        wl_kw["arrays"] = args.batch_arrays
+        if args.batch_config:
+            wl_kw["config"] = tuple(int(v) for v in args.batch_config.split(","))
+    kernels_list, meta, state = WORKLOADS[args.workload](B, W, torch, dev, rank, args.log2n, **wl_kw)
     stream = torch.cuda.current_stream()
 
     def step():

@@ -236,25 +236,30 @@ typedef struct ptrig_batch_plan ptrig_batch_plan;
 #define PTRIG_BATCH_GRAPH 1u /* ptrig_batch_run launches a captured CUDA graph */
 
 /* Builds a plan for `count` arrays from host descriptors (copied; the caller
- * may free host_descs afterwards).  The plan owns device copies of the
- * descriptors and a tile-to-array map; creating it calls cudaMalloc and a
- * synchronous copy.  Errors: NULL descriptor pointers with n > 0, unknown
- * func, nonzero reserved, or more than 2^32 tiles -> PTRIG_ERR_INVALID_ARG
- * (no plan is returned). */
+ * may free host_descs afterwards).  The plan cuts every array into tiles of
+ * block * items_per_thread elements (plus a head tile of at most three
+ * elements when the array's pointers share one misalignment inside a 16-byte
+ * line) and owns a device table of 32-byte tile descriptors, grouped by
+ * func; creating it calls cudaMalloc and a synchronous copy.  Errors: NULL
+ * descriptor pointers with n > 0, unknown func, nonzero reserved, or more
+ * than 2^31 - 1 tiles of one func -> PTRIG_ERR_INVALID_ARG (no plan is
+ * returned). */
 ptrig_status ptrig_batch_plan_create(ptrig_batch_plan **plan, const ptrig_desc *host_descs, size_t count,
                                      int flags);
 
-/* Runs the whole batch as one persistent kernel launch on `stream` (or one
- * graph launch with PTRIG_BATCH_GRAPH).  Captureable into a caller's CUDA
- * graph when the plan was built without PTRIG_BATCH_GRAPH. */
+/* Runs the whole batch on `stream`: one kernel launch per func present, one
+ * block per tile (or one graph launch with PTRIG_BATCH_GRAPH).  Captureable
+ * into a caller's CUDA graph when the plan was built without
+ * PTRIG_BATCH_GRAPH. */
 ptrig_status ptrig_batch_run(ptrig_batch_plan *plan, ptrig_stream stream);
 
 /* Baseline for comparison: the same work as one elementwise launch per array. */
 ptrig_status ptrig_batch_run_per_array(ptrig_batch_plan *plan, ptrig_stream stream);
 
-/* Sets the batch kernel's threads per block (64..1024, multiple of 32) and
- * elements per thread per tile (4..256, multiple of 4); rebuilds the tile map
- * (synchronous).  0 keeps the current value. */
+/* Sets the batch kernels' threads per block (64..512, multiple of 32) and
+ * elements per thread per tile (4..256, multiple of 4; default 128 x 16);
+ * rebuilds the tile table (synchronous).  0 keeps the current value.
+ * get_config also returns the tile count and the blocks launched per run. */
 ptrig_status ptrig_batch_plan_set_config(ptrig_batch_plan *plan, int block, int items_per_thread);
 ptrig_status ptrig_batch_plan_get_config(const ptrig_batch_plan *plan, int *block, int *items_per_thread,
                                          uint64_t *tiles, int *grid);

@@ -1,31 +1,50 @@
 // ptrig_batch.cu -- ragged batch: thousands of arrays, each with its own
-// function selector, evaluated by ONE persistent kernel launch.
+// function selector, evaluated by one kernel launch per selector.
 //
 // The plan cuts every array into tiles of block * items_per_thread elements
-// and keeps a tile -> array map in device memory, so a block finds its array
-// with a single load.  Blocks walk the tile list round-robin (tile = blockIdx,
-// blockIdx + grid, ...); a tile's selector is uniform over the block, so the
-// switch on it never diverges.  The grid is the SM count times the kernel's
-// occupancy.  With PTRIG_BATCH_GRAPH the launch is captured once into a CUDA
-// graph and ptrig_batch_run replays it.
+// and uploads, per selector, a list of 32-byte tile descriptors (pointers
+// already offset to the tile, and its length).  k_batch_tiles<OP> runs one
+// block per tile: a single broadcast load finds the tile, then the block
+// streams it with the inline vector code of the elementwise kernels (a ring of
+// four 16-byte loads per thread).  Many small resident blocks hide the memory
+// latency, as in the one-shot elementwise kernels, and no per-tile switch or
+// call remains.  An array whose pointers share one misalignment inside a
+// 16-byte line gets a separate head tile of at most three elements, so that
+// its other tiles start aligned.  With PTRIG_BATCH_GRAPH the four launches are
+// captured once into a CUDA graph and ptrig_batch_run replays it.
+//
+// The no-allocation entry point further below keeps a persistent kernel over
+// a per-array tile table that it builds on the device.
 #include <algorithm>
 #include <mutex>
 #include <vector>
 
 #include "ptrig_map.cuh"
 
+namespace ptrig {
+// One tile of one array: pointers offset to the tile's first element.
+struct BatchTile {
+  const float *x;
+  float *y0;
+  float *y1;  // sincos only
+  uint32_t len;
+  uint32_t pad;
+};
+static_assert(sizeof(BatchTile) == 32, "BatchTile layout");
+}  // namespace ptrig
+
 struct ptrig_batch_plan {
   int device = -1;
   unsigned flags = 0;
   std::vector<ptrig_desc> host;
-  ptrig_desc *d_desc = nullptr;
-  uint32_t *d_owner = nullptr;
-  size_t owner_cap = 0;
-  uint64_t *d_first = nullptr;
+  ptrig::BatchTile *d_tiles = nullptr;
+  size_t tiles_cap = 0;
+  uint64_t op_off[4] = {};  // first tile of each selector in d_tiles
+  uint64_t op_cnt[4] = {};  // tiles of each selector
   uint64_t ntiles = 0;
-  int block = 256;
-  int items = 32;
-  int grid = 0;
+  int block = 128;
+  int items = 16;
+  int grid = 0;  // blocks launched per run, over the four kernels
   cudaStream_t cap_stream = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -115,34 +134,51 @@ static __device__ __noinline__ void batch_tile(const ptrig_desc d, uint64_t star
   if (done < len) batch_elements<OP>(x, y0, y1, done, len, tab);
 }
 
-__global__ void __launch_bounds__(512, 2) k_batch(const ptrig_desc *__restrict__ descs,
-                                               const uint32_t *__restrict__ owner,
-                                               const uint64_t *__restrict__ first_tile, uint64_t ntiles,
-                                               uint32_t tile_elems) {
+// One block per tile of selector OP.  Vector path when the tile's pointers
+// are 16-byte aligned (a ring of four 16-byte loads per thread, the next load
+// of a slot issued before the slot's vector is computed); element path
+// otherwise and for the len % 4 tail; out-of-line full reduction after an
+// angle beyond 2^20, as in the elementwise kernels.
+template <int OP>
+__global__ void __launch_bounds__(512) k_batch_tiles(const BatchTile *__restrict__ tiles) {
+  using F = Proposed<OP>;
   __shared__ float4 s_tab[8];
   if (threadIdx.x < 8) s_tab[threadIdx.x] = c_tab_f32[threadIdx.x];
+  const BatchTile t = tiles[blockIdx.x];
   __syncthreads();
-  for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const uint32_t a = __ldg(owner + tile);
-    const ptrig_desc d = descs[a];
-    const uint64_t start = (tile - __ldg(first_tile + a)) * (uint64_t)tile_elems;
-    const uint64_t rem = d.n - start;
-    const uint32_t len = rem < tile_elems ? (uint32_t)rem : tile_elems;
-    switch (d.func) {
-      case PTRIG_SIN:
-        batch_tile<OP_SIN>(d, start, len, s_tab);
-        break;
-      case PTRIG_COS:
-        batch_tile<OP_COS>(d, start, len, s_tab);
-        break;
-      case PTRIG_TAN:
-        batch_tile<OP_TAN>(d, start, len, s_tab);
-        break;
-      default:
-        batch_tile<OP_SINCOS>(d, start, len, s_tab);
-        break;
+  float *y1 = (OP == OP_SINCOS) ? t.y1 : nullptr;
+  uintptr_t a = (uintptr_t)t.x | (uintptr_t)t.y0;
+  if (OP == OP_SINCOS) a |= (uintptr_t)y1;
+  const uint32_t nv = (a & 15u) ? 0u : t.len / 4u;
+  constexpr int R = 4;
+  const uint4 *xv = reinterpret_cast<const uint4 *>(t.x);
+  uint4 buf[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const uint32_t i = threadIdx.x + r * blockDim.x;
+    if (i < nv) buf[r] = ld_stream(xv + i);
+  }
+  uint32_t resume = 0;
+  for (uint32_t v0 = threadIdx.x; v0 < nv; v0 += R * blockDim.x) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const uint32_t i = v0 + r * blockDim.x;
+      if (i < nv) {
+        const uint4 cur = buf[r];
+        const uint32_t nx = i + R * blockDim.x;
+        if (nx < nv) buf[r] = ld_stream(xv + nx);
+        if (!map_vector_fast<float, F>(cur, i, t.y0, y1, s_tab)) {
+          resume = i + 1;
+          goto full;
+        }
+      }
     }
   }
+  goto tail;
+full:
+  batch_resume_full<OP>(t.x, t.y0, y1, resume - 1, nv, s_tab);
+tail:
+  if (nv * 4u < t.len) batch_elements<OP>(t.x, t.y0, y1, nv * 4u, t.len, s_tab);
 }
 
 // ---------------------------------------------------------------------------
@@ -265,11 +301,19 @@ static void free_graph(ptrig_batch_plan *p) {
   p->graph = nullptr;
 }
 
-static ptrig_status launch_batch(ptrig_batch_plan *p, cudaStream_t s) {
-  if (p->ntiles == 0) return PTRIG_OK;
-  k_batch<<<p->grid, p->block, 0, s>>>(p->d_desc, p->d_owner, p->d_first, p->ntiles,
-                                        (uint32_t)(p->block * p->items));
+template <int OP>
+static ptrig_status launch_batch_op(const ptrig_batch_plan *p, cudaStream_t s) {
+  if (p->op_cnt[OP] == 0) return PTRIG_OK;
+  k_batch_tiles<OP><<<(unsigned)p->op_cnt[OP], p->block, 0, s>>>(p->d_tiles + p->op_off[OP]);
   return finish_launch();
+}
+
+static ptrig_status launch_batch(ptrig_batch_plan *p, cudaStream_t s) {
+  ptrig_status st = launch_batch_op<OP_SIN>(p, s);
+  if (st == PTRIG_OK) st = launch_batch_op<OP_COS>(p, s);
+  if (st == PTRIG_OK) st = launch_batch_op<OP_TAN>(p, s);
+  if (st == PTRIG_OK) st = launch_batch_op<OP_SINCOS>(p, s);
+  return st;
 }
 
 static ptrig_status capture_graph(ptrig_batch_plan *p) {
@@ -291,43 +335,50 @@ static ptrig_status capture_graph(ptrig_batch_plan *p) {
   return PTRIG_OK;
 }
 
-// Rebuilds the tile map for the plan's (block, items) and uploads it.
+// Rebuilds the per-selector tile lists for the plan's (block, items) and
+// uploads them (synchronous).
 static ptrig_status build_tiles(ptrig_batch_plan *p) {
   const uint64_t tile = (uint64_t)p->block * (uint64_t)p->items;
-  std::vector<uint64_t> first(p->host.size() + 1);
+  std::vector<BatchTile> lists[4];
+  for (const ptrig_desc &d : p->host) {
+    if (d.n == 0) continue;
+    const int op = (int)d.func;
+    float *y1 = (op == OP_SINCOS) ? d.y1 : nullptr;
+    uint64_t off = 0;
+    const uintptr_t ox = (uintptr_t)d.x & 15u;
+    if (ox != 0 && (ox & 3u) == 0 && ((uintptr_t)d.y0 & 15u) == ox && (!y1 || ((uintptr_t)y1 & 15u) == ox)) {
+      off = std::min<uint64_t>(d.n, (16u - ox) / 4u);  // head tile up to the 16-byte boundary
+      lists[op].push_back(BatchTile{d.x, d.y0, y1, (uint32_t)off, 0u});
+    }
+    for (; off < d.n; off += tile) {
+      const uint64_t len = std::min<uint64_t>(tile, d.n - off);
+      lists[op].push_back(BatchTile{d.x + off, d.y0 + off, y1 ? y1 + off : nullptr, (uint32_t)len, 0u});
+    }
+  }
   uint64_t nt = 0;
-  for (size_t i = 0; i < p->host.size(); ++i) {
-    first[i] = nt;
-    nt += (p->host[i].n + tile - 1) / tile;
+  for (int op = 0; op < 4; ++op) {
+    if (lists[op].size() > 0x7fffffffull) return PTRIG_ERR_INVALID_ARG;  // grid limit
+    p->op_off[op] = nt;
+    p->op_cnt[op] = lists[op].size();
+    nt += lists[op].size();
   }
-  first[p->host.size()] = nt;
-  if (nt > 0xffffffffull) return PTRIG_ERR_INVALID_ARG;
-  std::vector<uint32_t> owner((size_t)nt);
-  for (size_t i = 0; i < p->host.size(); ++i)
-    for (uint64_t t = first[i]; t < first[i + 1]; ++t) owner[(size_t)t] = (uint32_t)i;
   cudaError_t e;
-  if (nt > p->owner_cap) {
-    if (p->d_owner) cudaFree(p->d_owner);
-    p->d_owner = nullptr;
-    p->owner_cap = 0;
-    e = cudaMalloc(&p->d_owner, std::max<size_t>((size_t)nt, 1) * sizeof(uint32_t));
+  if (nt > p->tiles_cap) {
+    if (p->d_tiles) cudaFree(p->d_tiles);
+    p->d_tiles = nullptr;
+    p->tiles_cap = 0;
+    e = cudaMalloc(&p->d_tiles, (size_t)nt * sizeof(BatchTile));
     if (e != cudaSuccess) return cuda_fail(e);
-    p->owner_cap = (size_t)nt;
+    p->tiles_cap = (size_t)nt;
   }
-  if (nt > 0) {
-    e = cudaMemcpy(p->d_owner, owner.data(), (size_t)nt * sizeof(uint32_t), cudaMemcpyHostToDevice);
+  for (int op = 0; op < 4; ++op) {
+    if (lists[op].empty()) continue;
+    e = cudaMemcpy(p->d_tiles + p->op_off[op], lists[op].data(), lists[op].size() * sizeof(BatchTile),
+                   cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e);
   }
-  e = cudaMemcpy(p->d_first, first.data(), first.size() * sizeof(uint64_t), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return cuda_fail(e);
   p->ntiles = nt;
-  int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch, p->block, 0);
-  if (e != cudaSuccess) return cuda_fail(e);
-  const int sms = sm_count();
-  if (sms <= 0) return PTRIG_ERR_NO_DEVICE;
-  const uint64_t g = std::min<uint64_t>((uint64_t)sms * (uint64_t)std::max(occ, 1), std::max<uint64_t>(nt, 1));
-  p->grid = (int)g;
+  p->grid = (int)std::min<uint64_t>(nt, 0x7fffffffull);
   return capture_graph(p);
 }
 
@@ -355,14 +406,6 @@ ptrig_status ptrig_batch_plan_create(ptrig_batch_plan **plan, const ptrig_desc *
   p->flags = (unsigned)flags;
   cudaGetDevice(&p->device);
   p->host.assign(host_descs, host_descs + count);
-  cudaError_t e = cudaMalloc(&p->d_desc, std::max<size_t>(count, 1) * sizeof(ptrig_desc));
-  if (e == cudaSuccess) e = cudaMalloc(&p->d_first, (count + 1) * sizeof(uint64_t));
-  if (e == cudaSuccess && count > 0)
-    e = cudaMemcpy(p->d_desc, p->host.data(), count * sizeof(ptrig_desc), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) {
-    ptrig_batch_plan_destroy(p);
-    return cuda_fail(e);
-  }
   const ptrig_status st = build_tiles(p);
   if (st != PTRIG_OK) {
     ptrig_batch_plan_destroy(p);
@@ -417,8 +460,8 @@ ptrig_status ptrig_batch_plan_autotune(ptrig_batch_plan *plan, ptrig_stream stre
                                        const int *cand_block, const int *cand_items, int ncand,
                                        int *best_block, int *best_items, float *best_ms) {
   if (!plan || reps < 1 || ncand < 0 || (ncand > 0 && (!cand_block || !cand_items))) return PTRIG_ERR_INVALID_ARG;
-  static const int kBlocks[] = {128, 256, 256, 512, 512, 256, 128, 512};
-  static const int kItems[] = {32, 16, 32, 8, 16, 64, 64, 32};
+  static const int kBlocks[] = {128, 128, 256, 256, 128, 512, 256, 128};
+  static const int kItems[] = {16, 32, 16, 32, 64, 16, 8, 8};
   const int nc = ncand ? ncand : (int)(sizeof(kBlocks) / sizeof(kBlocks[0]));
   const int *cb = ncand ? cand_block : kBlocks;
   const int *ci = ncand ? cand_items : kItems;
@@ -495,9 +538,7 @@ void ptrig_batch_plan_destroy(ptrig_batch_plan *plan) {
   if (!plan) return;
   free_graph(plan);
   if (plan->cap_stream) cudaStreamDestroy(plan->cap_stream);
-  if (plan->d_desc) cudaFree(plan->d_desc);
-  if (plan->d_owner) cudaFree(plan->d_owner);
-  if (plan->d_first) cudaFree(plan->d_first);
+  if (plan->d_tiles) cudaFree(plan->d_tiles);
   delete plan;
 }
 

@@ -401,34 +401,47 @@ def test_half_vector_and_scalar_paths_agree(B, dt):
 
 def _make_batch(n_arrays=60, seed=3):
     r = np.random.default_rng(seed)
-    lengths = list(r.integers(0, 20000, n_arrays)) + [0, 1, 3, 5, 4096, 65537]
+    lengths = list(r.integers(0, 20000, n_arrays)) + [0, 1, 3, 5, 4096, 65537, 2047, 2049]
     funcs = list(r.integers(0, 4, len(lengths)))
     offs = list(r.integers(0, 4, len(lengths)))
-    return lengths, funcs, offs
+    # output offsets: equal to the input's (congruent misalignment) for most
+    # arrays, different for every fifth (element path throughout)
+    yoffs = [o if i % 5 else (o + 1 + i) % 4 for i, o in enumerate(offs)]
+    return lengths, funcs, offs, yoffs
+
+
+GUARD = 8
 
 
 def test_batch_matches_single_kernels_and_oracle(B, oracle):
-    lengths, funcs, offs = _make_batch()
-    xs, ys, zs, descs, keep = [], [], [], [], []
-    for i, (n, f, o) in enumerate(zip(lengths, funcs, offs)):
+    lengths, funcs, offs, yoffs = _make_batch()
+    xs, ys, zs, descs, bufs = [], [], [], [], []
+    for i, (n, f, o, oy) in enumerate(zip(lengths, funcs, offs, yoffs)):
         xh = workloads.batch_array(i, n)
-        xb = _dev(np.concatenate([np.zeros(o, np.float32), xh]))
-        yb = torch.full_like(xb, -5.0)
-        zb = torch.full_like(xb, -5.0)
-        x, y, z = xb[o:], yb[o:], zb[o:]
-        keep.append((xb, yb, zb))
+        xb = _dev(np.concatenate([np.zeros(o, np.float32), xh, np.zeros(GUARD, np.float32)]))
+        yb = torch.full((oy + n + GUARD,), -5.0, dtype=torch.float32, device="cuda")
+        zb = torch.full_like(yb, -5.0)
+        x, y, z = xb[o:o + n], yb[oy:oy + n], zb[oy:oy + n]
+        bufs.append((yb, zb, oy))
         xs.append(xh)
         ys.append(y)
         zs.append(z)
         descs.append((x, y, z if f == 3 else None, n, f))
     for flags in (0, B.BATCH_GRAPH):
-        for y in ys:
-            y.fill_(-5.0)
+        for yb, zb, _ in bufs:
+            yb.fill_(-5.0)
+            zb.fill_(-5.0)
         plan = B.BatchPlan(descs, flags)
         plan.set_config(128, 8)
         plan.run()
         torch.cuda.synchronize()
         for i, (n, f) in enumerate(zip(lengths, funcs)):
+            yb, zb, oy = bufs[i]
+            for buf in (yb, zb):  # nothing written outside each array
+                hb = buf.cpu().numpy()
+                assert np.all(hb[:oy] == -5.0) and np.all(hb[oy + n:] == -5.0), (i, n, f)
+            if f != 3:
+                assert np.all(zb.cpu().numpy() == -5.0)
             if n == 0:
                 continue
             got = ys[i].cpu().numpy()[:n]
