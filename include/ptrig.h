@@ -242,21 +242,19 @@ typedef struct ptrig_batch_plan ptrig_batch_plan;
  * line) and owns a device table of 32-byte tile descriptors, grouped by
  * func; creating it calls cudaMalloc and a synchronous copy.  Errors: NULL
  * descriptor pointers with n > 0, unknown func, nonzero reserved, or more
- * than 2^31 - 1 tiles of one func -> PTRIG_ERR_INVALID_ARG (no plan is
- * returned). */
+ * than 2^31 - 1 tiles -> PTRIG_ERR_INVALID_ARG (no plan is returned). */
 ptrig_status ptrig_batch_plan_create(ptrig_batch_plan **plan, const ptrig_desc *host_descs, size_t count,
                                      int flags);
 
-/* Runs the whole batch on `stream`: one kernel launch per func present, one
- * block per tile (or one graph launch with PTRIG_BATCH_GRAPH).  Captureable
- * into a caller's CUDA graph when the plan was built without
- * PTRIG_BATCH_GRAPH. */
+/* Runs the whole batch on `stream` as one kernel launch, one block per tile
+ * (or one graph launch with PTRIG_BATCH_GRAPH).  Captureable into a caller's
+ * CUDA graph when the plan was built without PTRIG_BATCH_GRAPH. */
 ptrig_status ptrig_batch_run(ptrig_batch_plan *plan, ptrig_stream stream);
 
 /* Baseline for comparison: the same work as one elementwise launch per array. */
 ptrig_status ptrig_batch_run_per_array(ptrig_batch_plan *plan, ptrig_stream stream);
 
-/* Sets the batch kernels' threads per block (64..512, multiple of 32) and
+/* Sets the batch kernel's threads per block (64..512, multiple of 32) and
  * elements per thread per tile (4..256, multiple of 4; default 128 x 16);
  * rebuilds the tile table (synchronous).  0 keeps the current value.
  * get_config also returns the tile count and the blocks launched per run. */

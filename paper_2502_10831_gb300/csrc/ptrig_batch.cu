@@ -1,16 +1,17 @@
 // ptrig_batch.cu -- ragged batch: thousands of arrays, each with its own
-// function selector, evaluated by one kernel launch per selector.
+// function selector, evaluated by one kernel launch.
 //
 // The plan cuts every array into tiles of block * items_per_thread elements
-// and uploads, per selector, a list of 32-byte tile descriptors (pointers
-// already offset to the tile, and its length).  k_batch_tiles<OP> runs one
-// block per tile: a single broadcast load finds the tile, then the block
-// streams it with the inline vector code of the elementwise kernels (a ring of
-// four 16-byte loads per thread).  Many small resident blocks hide the memory
-// latency, as in the one-shot elementwise kernels, and no per-tile switch or
-// call remains.  An array whose pointers share one misalignment inside a
+// and uploads a table of 32-byte tile descriptors (pointers already offset to
+// the tile, and its length), grouped by selector.  k_batch_tiles runs one
+// block per tile: a single broadcast load finds the tile, the block index
+// range gives its selector (uniform over the block), and the block streams the
+// tile with the inline vector code of the elementwise kernels (a ring of four
+// 16-byte loads per thread).  Many small resident blocks hide the memory
+// latency, as in the one-shot elementwise kernels, and no per-tile call
+// remains.  An array whose pointers share one misalignment inside a
 // 16-byte line gets a separate head tile of at most three elements, so that
-// its other tiles start aligned.  With PTRIG_BATCH_GRAPH the four launches are
+// its other tiles start aligned.  With PTRIG_BATCH_GRAPH the launch is
 // captured once into a CUDA graph and ptrig_batch_run replays it.
 //
 // The no-allocation entry point further below keeps a persistent kernel over
@@ -44,7 +45,7 @@ struct ptrig_batch_plan {
   uint64_t ntiles = 0;
   int block = 128;
   int items = 16;
-  int grid = 0;  // blocks launched per run, over the four kernels
+  int grid = 0;  // blocks launched per run (one per tile)
   cudaStream_t cap_stream = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -134,18 +135,14 @@ static __device__ __noinline__ void batch_tile(const ptrig_desc d, uint64_t star
   if (done < len) batch_elements<OP>(x, y0, y1, done, len, tab);
 }
 
-// One block per tile of selector OP.  Vector path when the tile's pointers
+// One tile of selector OP by one block.  Vector path when the tile's pointers
 // are 16-byte aligned (a ring of four 16-byte loads per thread, the next load
 // of a slot issued before the slot's vector is computed); element path
 // otherwise and for the len % 4 tail; out-of-line full reduction after an
 // angle beyond 2^20, as in the elementwise kernels.
 template <int OP>
-__global__ void __launch_bounds__(512) k_batch_tiles(const BatchTile *__restrict__ tiles) {
+__device__ __forceinline__ void batch_block(const BatchTile &t, const float4 *s_tab) {
   using F = Proposed<OP>;
-  __shared__ float4 s_tab[8];
-  if (threadIdx.x < 8) s_tab[threadIdx.x] = c_tab_f32[threadIdx.x];
-  const BatchTile t = tiles[blockIdx.x];
-  __syncthreads();
   float *y1 = (OP == OP_SINCOS) ? t.y1 : nullptr;
   uintptr_t a = (uintptr_t)t.x | (uintptr_t)t.y0;
   if (OP == OP_SINCOS) a |= (uintptr_t)y1;
@@ -179,6 +176,26 @@ full:
   batch_resume_full<OP>(t.x, t.y0, y1, resume - 1, nv, s_tab);
 tail:
   if (nv * 4u < t.len) batch_elements<OP>(t.x, t.y0, y1, nv * 4u, t.len, s_tab);
+}
+
+// One launch for the whole batch: the tiles are stored by selector (sin,
+// cos, tan, sincos), and block b takes tile b with the selector whose range
+// holds b -- uniform over the block, so the branch never diverges.
+__global__ void __launch_bounds__(512) k_batch_tiles(const BatchTile *__restrict__ tiles, uint32_t end_sin,
+                                                     uint32_t end_cos, uint32_t end_tan) {
+  __shared__ float4 s_tab[8];
+  if (threadIdx.x < 8) s_tab[threadIdx.x] = c_tab_f32[threadIdx.x];
+  const uint32_t b = blockIdx.x;
+  const BatchTile t = tiles[b];
+  __syncthreads();
+  if (b < end_sin)
+    batch_block<OP_SIN>(t, s_tab);
+  else if (b < end_cos)
+    batch_block<OP_COS>(t, s_tab);
+  else if (b < end_tan)
+    batch_block<OP_TAN>(t, s_tab);
+  else
+    batch_block<OP_SINCOS>(t, s_tab);
 }
 
 // ---------------------------------------------------------------------------
@@ -301,19 +318,12 @@ static void free_graph(ptrig_batch_plan *p) {
   p->graph = nullptr;
 }
 
-template <int OP>
-static ptrig_status launch_batch_op(const ptrig_batch_plan *p, cudaStream_t s) {
-  if (p->op_cnt[OP] == 0) return PTRIG_OK;
-  k_batch_tiles<OP><<<(unsigned)p->op_cnt[OP], p->block, 0, s>>>(p->d_tiles + p->op_off[OP]);
-  return finish_launch();
-}
-
 static ptrig_status launch_batch(ptrig_batch_plan *p, cudaStream_t s) {
-  ptrig_status st = launch_batch_op<OP_SIN>(p, s);
-  if (st == PTRIG_OK) st = launch_batch_op<OP_COS>(p, s);
-  if (st == PTRIG_OK) st = launch_batch_op<OP_TAN>(p, s);
-  if (st == PTRIG_OK) st = launch_batch_op<OP_SINCOS>(p, s);
-  return st;
+  if (p->ntiles == 0) return PTRIG_OK;
+  k_batch_tiles<<<(unsigned)p->ntiles, p->block, 0, s>>>(
+      p->d_tiles, (uint32_t)p->op_cnt[0], (uint32_t)(p->op_cnt[0] + p->op_cnt[1]),
+      (uint32_t)(p->op_cnt[0] + p->op_cnt[1] + p->op_cnt[2]));
+  return finish_launch();
 }
 
 static ptrig_status capture_graph(ptrig_batch_plan *p) {
@@ -357,11 +367,11 @@ static ptrig_status build_tiles(ptrig_batch_plan *p) {
   }
   uint64_t nt = 0;
   for (int op = 0; op < 4; ++op) {
-    if (lists[op].size() > 0x7fffffffull) return PTRIG_ERR_INVALID_ARG;  // grid limit
     p->op_off[op] = nt;
     p->op_cnt[op] = lists[op].size();
     nt += lists[op].size();
   }
+  if (nt > 0x7fffffffull) return PTRIG_ERR_INVALID_ARG;  // one block per tile: grid limit
   cudaError_t e;
   if (nt > p->tiles_cap) {
     if (p->d_tiles) cudaFree(p->d_tiles);
