@@ -139,9 +139,22 @@ def oracle_rate(x_host, seconds_budget: float = 12.0, threads: int | None = None
         list(ex.map(work, parts))
     dt = time.perf_counter() - t0
     evals = 7 * m
+    # one core, and a float64 libm-class implementation (numpy) for context
+    m1 = min(x_host.size, 1 << 20)
+    t0 = time.perf_counter()
+    work(xd[:m1])
+    one = 7 * m1 / (time.perf_counter() - t0) / 1e9
+    t0 = time.perf_counter()
+    np.sin(xd)
+    np.cos(xd)
+    np.tan(xd)
+    lib = 3 * m / (time.perf_counter() - t0) / 1e9
     return {"value": evals / dt / 1e9, "unit": "Gelem/s", "cores": threads, "kind": "oracle",
             "sample": f"first {m} angles of the workload x 7 functions (sincos counted once), "
-                      f"{threads} threads, {dt:.2f} s wall"}
+                      f"{threads} threads, {dt:.2f} s wall",
+            "one_core": {"value": round(one, 5), "sample": f"first {m1} angles x 7 functions, 1 thread"},
+            "numpy_f64_sin_cos_tan_one_core": {"value": round(lib, 4),
+                                               "note": "context: numpy float64 sin/cos/tan, not the method"}}
 
 
 def cpu_simd_rate(x_host):
@@ -446,9 +459,10 @@ def main():
                 "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "algorithmic_bytes_per_launch": dom.nbytes, "traffic": traffic}
     config = {"workload": meta["workload"], "n_per_gpu": meta["n_per_gpu"], "l2": meta["l2"],
-              "launch_config_f32": B.ptrig_get_launch_config(B.FAMILY_F32),
-              "launch_config_half": B.ptrig_get_launch_config(B.FAMILY_HALF),
-              "launch_config_taylor": B.ptrig_get_launch_config(B.FAMILY_TAYLOR)}
+              "launch_configs": {name: B.ptrig_get_launch_config(fam) for name, fam in (
+                  ("f32", B.FAMILY_F32), ("f32_sincos", B.FAMILY_F32_SINCOS), ("taylor", B.FAMILY_TAYLOR),
+                  ("half", B.FAMILY_HALF), ("half_sincos", B.FAMILY_HALF_SINCOS), ("bf16", B.FAMILY_BF16),
+                  ("bf16_sincos", B.FAMILY_BF16_SINCOS), ("bwd", B.FAMILY_BWD))}}
     if "autotuned" in meta:
         config["batch_autotuned"] = meta["autotuned"]
     line = {"metric": meta["metric"], "value": round(value, 2), "unit": "Gelem/s", "n_gpus": world,
@@ -642,14 +656,30 @@ def e2e(B, x_host, n, device, stream):
             fn()
         torch.cuda.synchronize()
         res[mode] = (time.perf_counter() - t0) / reps
+    # the host link alone: one pinned copy of the angle array each way
+    def link(fn):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        return 4 * n * 3 / (time.perf_counter() - t0) / 1e9
+
+    h2d = link(lambda: dx.copy_(hx, non_blocking=True))
+    d2h = link(lambda: hy[0].copy_(douts[0], non_blocking=True))
     del douts
     best = min(res, key=res.get)
     dt = res[best]
+    bound_s = 8 * 4 * n / (d2h * 1e9)  # the step's device-to-host bytes at the link's copy rate
     return {"value": round(7 * n / dt / 1e9, 2), "unit": "Gelem/s", "h2d_bytes_per_step": 4 * n,
             "d2h_bytes_per_step": 8 * 4 * n, "ms_per_step": round(dt * 1e3, 3), "mode": best,
             "ms_per_step_by_mode": {k: round(v * 1e3, 3) for k, v in res.items()},
+            "link_gbs": {"h2d": round(h2d, 1), "d2h": round(d2h, 1)},
+            "link_bound_ms": round(bound_s * 1e3, 3), "link_frac": round(bound_s / dt, 4),
             "how": "pinned host angles -> device, the 7 kernels of the step, all 8 output arrays back in pinned "
-                   "host memory; timed with the host clock around synchronized steps"}
+                   "host memory; timed with the host clock around synchronized steps.  link_frac = the step's "
+                   "device-to-host bytes at the measured pinned-copy rate / the measured step time"}
 
 
 if __name__ == "__main__":

@@ -194,13 +194,16 @@ ptrig_status ptrig_cudamath_f32(int func, int fast, const float *x, float *y0, f
 
 /* Kernel families for ptrig_set_launch_config. */
 typedef enum ptrig_family {
-  PTRIG_FAMILY_F32 = 0,      /* proposed FP32, all functions */
-  PTRIG_FAMILY_HALF = 1,     /* fp16 storage */
-  PTRIG_FAMILY_TAYLOR = 2,   /* Taylor-n FP32 */
-  PTRIG_FAMILY_BWD = 3,      /* FP32 derivatives */
-  PTRIG_FAMILY_BF16 = 4,     /* bf16 storage */
-  PTRIG_FAMILY_CUDAMATH = 5, /* ptrig_cudamath_f32 comparison kernels */
-  PTRIG_FAMILY_COUNT = 6
+  PTRIG_FAMILY_F32 = 0,         /* proposed FP32 sin, cos, tan */
+  PTRIG_FAMILY_HALF = 1,        /* fp16 storage sin, cos, tan */
+  PTRIG_FAMILY_TAYLOR = 2,      /* Taylor-n FP32 */
+  PTRIG_FAMILY_BWD = 3,         /* FP32 derivatives */
+  PTRIG_FAMILY_BF16 = 4,        /* bf16 storage sin, cos, tan */
+  PTRIG_FAMILY_CUDAMATH = 5,    /* ptrig_cudamath_f32 comparison kernels */
+  PTRIG_FAMILY_F32_SINCOS = 6,  /* proposed FP32 sincos (two outputs) */
+  PTRIG_FAMILY_HALF_SINCOS = 7, /* fp16 sincos */
+  PTRIG_FAMILY_BF16_SINCOS = 8, /* bf16 sincos */
+  PTRIG_FAMILY_COUNT = 9
 } ptrig_family;
 
 /* Threads per block (64..512, multiple of 32), 16-byte loads kept in flight

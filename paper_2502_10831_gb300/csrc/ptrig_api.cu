@@ -66,14 +66,16 @@ int occupancy(const void *kernel, int block) {
   return nb;
 }
 
-// Defaults measured on GB300 (2^28 angles): the FP32, bf16, Taylor and
-// derivative kernels run 128 threads with four 16-byte loads in flight per
-// thread, one-shot (one contiguous 8 KiB chunk of input per block); fp16 the
-// same with eight loads in flight; CUDA's own math functions run best
-// persistent (512 threads, 8 blocks per SM).
+// Defaults measured on GB300 (2^28 angles, one sweep of every family): all
+// streaming kernels run one-shot (one contiguous chunk of block * vec_per_thread
+// vectors per block) with 64-thread blocks -- four 16-byte loads in flight per
+// thread for FP32 sin/cos/tan, Taylor, derivatives and bf16, eight for fp16,
+// two for the FP32 sincos (89 registers; smaller chunks keep more blocks
+// resident).  CUDA's own math functions run best persistent (512 threads, 8
+// blocks per SM).
 static std::mutex g_cfg_mu;
-static LaunchCfg g_cfg[PTRIG_FAMILY_COUNT] = {{128, 4, 0}, {128, 8, 0}, {128, 4, 0},
-                                               {128, 4, 0}, {128, 4, 0}, {512, 2, 8}};
+static LaunchCfg g_cfg[PTRIG_FAMILY_COUNT] = {{64, 4, 0},  {64, 8, 0}, {64, 4, 0}, {64, 4, 0}, {64, 4, 0},
+                                               {512, 2, 8}, {64, 2, 0}, {64, 8, 0}, {64, 4, 0}};
 
 LaunchCfg get_cfg(int family) {
   std::lock_guard<std::mutex> lk(g_cfg_mu);

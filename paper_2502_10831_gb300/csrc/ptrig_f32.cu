@@ -14,7 +14,7 @@ ptrig_status launch_proposed_f32(int op, const float *x, float *y0, float *y1, s
     case OP_TAN:
       return launch_map<float, Proposed<OP_TAN>>(PTRIG_FAMILY_F32, x, y0, y1, n, s);
     case OP_SINCOS:
-      return launch_map<float, Proposed<OP_SINCOS>>(PTRIG_FAMILY_F32, x, y0, y1, n, s);
+      return launch_map<float, Proposed<OP_SINCOS>>(PTRIG_FAMILY_F32_SINCOS, x, y0, y1, n, s);
     default:
       return PTRIG_ERR_INVALID_ARG;
   }

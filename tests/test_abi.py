@@ -68,7 +68,7 @@ def test_host_validation_without_gpu(lib):
     assert lib.ptrig_cudamath_f32(4, 0, 1024, 2048, None, 4, None) == 1
     assert lib.ptrig_set_launch_config(0, 100, 4, 0) == 1
     assert lib.ptrig_set_launch_config(0, 256, 3, 0) == 1
-    assert lib.ptrig_set_launch_config(7, 256, 4, 0) == 1
+    assert lib.ptrig_set_launch_config(9, 256, 4, 0) == 1
     assert lib.ptrig_set_launch_config(0, 256, 16, 0) == 1
 
 
@@ -81,13 +81,17 @@ def test_launch_config_roundtrip(lib):
 
 
 def test_default_launch_configs(lib):
-    """The per-family defaults picked by the GB300 sweeps (fp16 with eight
-    16-byte loads in flight, the other streaming families with four)."""
+    """The per-family defaults picked by the GB300 sweeps: one-shot 64-thread
+    blocks, eight 16-byte loads in flight for fp16, two for the FP32 sincos,
+    four otherwise; the CUDA-math comparison kernels persistent."""
     from paper_2502_10831_gb300 import binding as B
-    assert B.ptrig_get_launch_config(B.FAMILY_F32) == (128, 4, 0)
-    assert B.ptrig_get_launch_config(B.FAMILY_HALF) == (128, 8, 0)
-    assert B.ptrig_get_launch_config(B.FAMILY_BF16) == (128, 4, 0)
-    assert B.ptrig_get_launch_config(B.FAMILY_CUDAMATH) == (512, 2, 8)
+    want = {B.FAMILY_F32: (64, 4, 0), B.FAMILY_HALF: (64, 8, 0), B.FAMILY_TAYLOR: (64, 4, 0),
+            B.FAMILY_BWD: (64, 4, 0), B.FAMILY_BF16: (64, 4, 0), B.FAMILY_CUDAMATH: (512, 2, 8),
+            B.FAMILY_F32_SINCOS: (64, 2, 0), B.FAMILY_HALF_SINCOS: (64, 8, 0), B.FAMILY_BF16_SINCOS: (64, 4, 0)}
+    assert len(want) == B.FAMILY_COUNT
+    for fam, cfg in want.items():
+        assert B.ptrig_get_launch_config(fam) == cfg, fam
+    assert lib.ptrig_set_launch_config(B.FAMILY_COUNT, 64, 4, 0) == 1
 
 
 def test_batch_plan_rejects_bad_descriptors(lib):
