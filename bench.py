@@ -392,7 +392,10 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    Bld.build()
+    if local == 0:  # one build per node; the other ranks load what it wrote
+        Bld.build()
+    if dist:
+        dist.barrier()
     B.lib()
     dev = torch.device("cuda", local)
     wl_kw = {}
@@ -558,6 +561,12 @@ def extras(args, B, W, x, x_host, n, stream, peak, kernels):
             ms = _time_call(lambda: B.ptrig_cudamath_f32(fi, fast, x, y0, None, n, s_ptr), 5, stream)
             cm[("__" if fast else "") + f + "f"] = {"ms": round(ms, 4), "gelem_s": round(n / ms / 1e6, 2)}
     out["cuda_math"] = cm
+    tm = {}
+    for f in ("sin", "cos", "tan"):  # PyTorch's own elementwise kernels, for context
+        fn = getattr(torch, f)
+        ms = _time_call(lambda: fn(x, out=y0), 5, stream)
+        tm[f"torch.{f}"] = {"ms": round(ms, 4), "gelem_s": round(n / ms / 1e6, 2)}
+    out["torch_math"] = tm
     del y0, y1
     # packed half storage against the plain FP32 kernels
     half = {}
