@@ -100,9 +100,10 @@ template <int OP, int D>
 static void launch_bwd_d(const LaunchCfg &c, int sms, const float *x, const float *gy, float *gx, size_t n,
                          cudaStream_t s) {
   const size_t nvec = n / 4;
-  if (c.blocks_per_sm > 0) {
+  const bool oneshot = c.blocks_per_sm == 0 && (nvec + (size_t)c.block * D - 1) / ((size_t)c.block * D) <= INT_MAX;
+  if (!oneshot) {  // persistent (also past the one-shot grid limit)
     size_t g = (nvec + c.block - 1) / c.block;
-    const size_t cap = (size_t)sms * (size_t)c.blocks_per_sm;
+    const size_t cap = (size_t)sms * (size_t)(c.blocks_per_sm > 0 ? c.blocks_per_sm : 8);
     if (g > cap) g = cap;
     if (g < 1) g = 1;
     k_bwd<OP, D, true><<<(unsigned)g, c.block, 0, s>>>(x, gy, gx, n);

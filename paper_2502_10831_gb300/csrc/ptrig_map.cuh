@@ -213,9 +213,12 @@ inline size_t grid_for(size_t units, size_t per_block, const LaunchCfg &c, int s
 template <typename T, class F, int D>
 ptrig_status launch_map_d(const LaunchCfg &c, int sms, const T *x, T *y0, T *y1, size_t n, cudaStream_t s) {
   const size_t nvec = n / Storage<T>::EPV;
-  if (c.blocks_per_sm > 0) {  // persistent: blocks_per_sm resident blocks per SM
+  // one-shot needs one block per chunk; beyond the grid limit the persistent
+  // grid (8 blocks per SM) walks the array instead
+  const bool oneshot = c.blocks_per_sm == 0 && (nvec + (size_t)c.block * D - 1) / ((size_t)c.block * D) <= INT_MAX;
+  if (!oneshot) {  // persistent: blocks_per_sm resident blocks per SM
     size_t g = (nvec + c.block - 1) / c.block;
-    const size_t cap = (size_t)sms * (size_t)c.blocks_per_sm;
+    const size_t cap = (size_t)sms * (size_t)(c.blocks_per_sm > 0 ? c.blocks_per_sm : 8);
     if (g > cap) g = cap;
     if (g < 1) g = 1;
     launch_k_map<T, F, D, true>((unsigned)g, c.block, s, x, y0, y1, n);
