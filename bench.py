@@ -588,6 +588,21 @@ def extras(args, B, W, x, x_host, n, stream, peak, kernels):
     out["packed_half"] = half
     del xh16, xbf, h0, h1
     torch.cuda.empty_cache()
+    # FP64 data path (Sec. 4 evaluates in double) and the paper-faithful FP64
+    # kernels, on 2^26 doubles of the same workload: FP64-issue-bound on GB300
+    m = min(n, 1 << 26)
+    xd = x[:m].double()
+    yd = torch.empty_like(xd)
+    f64 = {}
+    for f in ("sin", "cos", "tan"):
+        ms = _time_call(lambda: getattr(B, f"ptrig_{f}_f64")(xd, yd, m, s_ptr), 5, stream)
+        f64[f"{f}_f64"] = {"ms": round(ms, 4), "gelem_s": round(m / ms / 1e6, 2)}
+    for fi, f in enumerate(("sin", "cos", "tan")):
+        ms = _time_call(lambda: B.ptrig_faithful_f64(fi, xd, yd, m, s_ptr), 5, stream)
+        f64[f"faithful_{f}_f64"] = {"ms": round(ms, 4), "gelem_s": round(m / ms / 1e6, 2)}
+    out["fp64"] = {"n": m, "kernels": f64, "bound": "FP64 issue (GB300 runs FP64 at a small fraction of FP32)"}
+    del xd, yd
+    torch.cuda.empty_cache()
     out["e2e"] = e2e(B, x_host, n, x.device, stream)
     out["cpu_baseline"] = oracle_rate(x_host)
     out["cpu_simd"] = cpu_simd_rate(x_host)

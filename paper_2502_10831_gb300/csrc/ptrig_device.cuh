@@ -50,6 +50,19 @@ __device__ __forceinline__ void st_stream(void *p, uint4 v) {
                : "memory");
 }
 
+// 32-byte forms (sm_100+ .v8 accesses); p must be 32-byte aligned.
+__device__ __forceinline__ void ld_stream32(const void *p, uint4 &a, uint4 &b) {
+  asm("ld.global.nc.L1::no_allocate.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
+      : "l"(p));
+}
+
+__device__ __forceinline__ void st_stream32(void *p, uint4 a, uint4 b) {
+  asm volatile("st.global.cs.v8.u32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(a.x), "r"(a.y),
+               "r"(a.z), "r"(a.w), "r"(b.x), "r"(b.y), "r"(b.z), "r"(b.w)
+               : "memory");
+}
+
 // ------------------------------------------------------------- MUFU helpers
 
 // h^2 = N^2 + D^2 lies in [8e4, 4e6] for every table row, so the flush-to-zero
@@ -315,6 +328,8 @@ struct Proposed {
   static constexpr int NOUT = (OP == OP_SINCOS) ? 2 : 1;
   static constexpr bool HAS_SLOW = true;
   static constexpr bool HAS_PAIR = true;
+  static constexpr bool USES_TABLE = true;  // coefficient table in shared memory
+  static constexpr int GROUP = 1;           // 16-byte accesses (32-byte ones measured slower)
   __device__ __forceinline__ static void eval_pair_mag(float2 x, const float4 *tab, float2 &m0, float2 &m1,
                                                        uint32_t &s0, uint32_t &s1) {
     proposed_pair_mag<OP>(x, tab, m0, m1, s0, s1);
@@ -358,6 +373,8 @@ struct Taylor {
   static constexpr int NOUT = 1;
   static constexpr bool HAS_SLOW = true;
   static constexpr bool HAS_PAIR = false;
+  static constexpr bool USES_TABLE = false;
+  static constexpr int GROUP = 2;  // 32-byte accesses
   __device__ __forceinline__ static void eval_pair_mag(float2, const float4 *, float2 &, float2 &, uint32_t &,
                                                        uint32_t &) {}
   template <bool FULL = true>

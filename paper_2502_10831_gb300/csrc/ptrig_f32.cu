@@ -54,6 +54,8 @@ struct CudaMath {
   static constexpr int NOUT = (OP == OP_SINCOS) ? 2 : 1;
   static constexpr bool HAS_SLOW = false;
   static constexpr bool HAS_PAIR = false;
+  static constexpr bool USES_TABLE = false;
+  static constexpr int GROUP = 2;
   __device__ __forceinline__ static void eval_pair_mag(float2, const float4 *, float2 &, float2 &, uint32_t &,
                                                        uint32_t &) {}
   template <bool FULL = true>

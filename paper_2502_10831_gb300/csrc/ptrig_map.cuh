@@ -87,6 +87,65 @@ static __device__ __noinline__ void map_resume_full(const T *__restrict__ x, T *
   }
 }
 
+// 32-byte groups for functors without the coefficient table and without the
+// 16-bit pair form: the output words of one 16-byte vector with the FP32
+// reduction, stored by the caller; false (outputs unset) when an element needs
+// the full reduction.
+template <typename T, class F>
+__device__ __forceinline__ bool wide_vector_eval(uint4 v, uint4 &o0, uint4 &o1) {
+  static_assert(!F::USES_TABLE && !F::HAS_PAIR, "wide groups take table-free scalar functors");
+  using S = Storage<T>;
+  constexpr int E = S::EPV;
+  float f[E];
+  S::unpack(v, f);
+  if constexpr (F::HAS_SLOW) {
+    bool slow = false;
+#pragma unroll
+    for (int e = 0; e < E; ++e) slow |= needs_slow(f[e]);
+    if (slow) return false;
+  }
+  float r0[E], r1[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) F::template eval<false>(f[e], nullptr, r0[e], r1[e]);
+  o0 = S::pack(r0);
+  if constexpr (F::NOUT == 2) o1 = S::pack(r1);
+  return true;
+}
+
+// Groups u, u + stride, ... < nu of two 16-byte vectors each, with the full
+// reduction; out of line like map_resume_full.
+template <typename T, class F>
+static __device__ __noinline__ void wide_resume_full(const T *__restrict__ x, T *__restrict__ y0,
+                                                     T *__restrict__ y1, size_t u, size_t nu, size_t stride) {
+  using S = Storage<T>;
+  constexpr int E = S::EPV;
+  for (; u < nu; u += stride) {
+    for (int w = 0; w < 2; ++w) {
+      const size_t i = 2 * u + w;
+      float f[E], o0[E], o1[E];
+      S::unpack(ld_stream(reinterpret_cast<const uint4 *>(x) + i), f);
+      for (int e = 0; e < E; ++e) F::template eval<true>(f[e], nullptr, o0[e], o1[e]);
+      st_stream(reinterpret_cast<uint4 *>(y0) + i, S::pack(o0));
+      if constexpr (F::NOUT == 2) st_stream(reinterpret_cast<uint4 *>(y1) + i, S::pack(o1));
+    }
+  }
+}
+
+// Two consecutive 16-byte vectors moved as one 32-byte access.
+struct Vec32 {
+  uint4 a[2];
+};
+
+__device__ __forceinline__ Vec32 ld_group32(const void *base, size_t u) {
+  Vec32 v;
+  ld_stream32(reinterpret_cast<const uint4 *>(base) + 2 * u, v.a[0], v.a[1]);
+  return v;
+}
+
+__device__ __forceinline__ void st_group32(void *base, size_t u, const Vec32 &v) {
+  st_stream32(reinterpret_cast<uint4 *>(base) + 2 * u, v.a[0], v.a[1]);
+}
+
 // Software-pipelined stream of 16-byte vectors.  Thread t of block b handles
 // vectors base, base + step, ... below `end`, keeping a ring of D loads in
 // flight: the slot of the vector about to be computed is refilled with the
@@ -155,10 +214,79 @@ full:
   map_resume_full<T, F>(x, y0, y1, resume - 1, end, step, s_tab);
 }
 
+// The same stream over 32-byte groups (two 16-byte vectors per access), for
+// functors without the coefficient table (F::USES_TABLE == false): no table
+// staging and no barrier; the n % E tail goes last.  For the table-using
+// functors 32-byte accesses measured slower, so they keep map_stream.
 template <typename T, class F, int D, bool PERSIST>
+__device__ __forceinline__ void map_stream_wide(const T *__restrict__ x, T *__restrict__ y0,
+                                                T *__restrict__ y1, size_t n) {
+  static_assert(!F::USES_TABLE, "32-byte groups are for functors without the table");
+  using S = Storage<T>;
+  constexpr int E = S::EPV * 2;  // elements per group
+  const size_t ng = n / E;
+  size_t i, step, end;
+  if (PERSIST) {
+    i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    step = (size_t)gridDim.x * blockDim.x;
+    end = ng;
+  } else {
+    const size_t chunk = (size_t)blockIdx.x * blockDim.x * D;
+    i = chunk + threadIdx.x;
+    step = blockDim.x;
+    end = chunk + (size_t)blockDim.x * D;
+    if (end > ng) end = ng;
+  }
+  size_t resume = 0;
+  Vec32 buf[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const size_t j = i + (size_t)d * step;
+    if (j < end) buf[d] = ld_group32(x, j);
+  }
+  for (; i < end; i += (size_t)D * step) {
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const size_t ii = i + (size_t)d * step;
+      if (ii < end) {
+        const Vec32 cur = buf[d];
+        if (PERSIST) {
+          const size_t jn = ii + (size_t)D * step;
+          if (jn < end) buf[d] = ld_group32(x, jn);
+        }
+        Vec32 o0, o1;
+        const bool ok = wide_vector_eval<T, F>(cur.a[0], o0.a[0], o1.a[0]) &
+                        wide_vector_eval<T, F>(cur.a[1], o0.a[1], o1.a[1]);
+        if (!ok) {
+          resume = ii + 1;  // +1 so that 0 means "finished"
+          goto full;
+        }
+        st_group32(y0, ii, o0);
+        if constexpr (F::NOUT == 2) st_group32(y1, ii, o1);
+      }
+    }
+  }
+  goto tail;
+full:
+  wide_resume_full<T, F>(x, y0, y1, resume - 1, end, step);
+tail:
+  if (blockIdx.x == 0) {  // the n % E elements after the last whole group
+    for (size_t k = ng * E + threadIdx.x; k < n; k += blockDim.x) {
+      float o0, o1;
+      F::template eval<true>(S::load1(x + k), nullptr, o0, o1);
+      S::store1(y0 + k, o0);
+      if constexpr (F::NOUT == 2) S::store1(y1 + k, o1);
+    }
+  }
+}
+
+template <typename T, class F, int D, bool PERSIST, int W>
 __global__ void __launch_bounds__(512) k_map(const T *__restrict__ x, T *__restrict__ y0, T *__restrict__ y1,
                                              size_t n) {
-  map_stream<T, F, D, PERSIST>(x, y0, y1, n);
+  if constexpr (W == 2)
+    map_stream_wide<T, F, D, PERSIST>(x, y0, y1, n);
+  else
+    map_stream<T, F, D, PERSIST>(x, y0, y1, n);
 }
 
 // Single-output functions on 16-bit storage are instruction-bound: this
@@ -166,21 +294,24 @@ __global__ void __launch_bounds__(512) k_map(const T *__restrict__ x, T *__restr
 // resident warps.  FP32 is memory-bound and sincos would spill, so both keep
 // k_map; on GB300 even a minimum of one block per SM in the launch bounds
 // slowed the FP32 kernels by 5-10% at the same register count.
-template <typename T, class F, int D, bool PERSIST>
+template <typename T, class F, int D, bool PERSIST, int W>
 __global__ void __launch_bounds__(512, 2) k_map_capped(const T *__restrict__ x, T *__restrict__ y0,
                                                        T *__restrict__ y1, size_t n) {
-  map_stream<T, F, D, PERSIST>(x, y0, y1, n);
+  if constexpr (W == 2)
+    map_stream_wide<T, F, D, PERSIST>(x, y0, y1, n);
+  else
+    map_stream<T, F, D, PERSIST>(x, y0, y1, n);
 }
 
 template <typename T, class F>
 constexpr bool map_capped() { return sizeof(T) == 2 && F::NOUT == 1; }
 
-template <typename T, class F, int D, bool PERSIST>
+template <typename T, class F, int D, bool PERSIST, int W>
 void launch_k_map(unsigned grid, int block, cudaStream_t s, const T *x, T *y0, T *y1, size_t n) {
   if constexpr (map_capped<T, F>())
-    k_map_capped<T, F, D, PERSIST><<<grid, block, 0, s>>>(x, y0, y1, n);
+    k_map_capped<T, F, D, PERSIST, W><<<grid, block, 0, s>>>(x, y0, y1, n);
   else
-    k_map<T, F, D, PERSIST><<<grid, block, 0, s>>>(x, y0, y1, n);
+    k_map<T, F, D, PERSIST, W><<<grid, block, 0, s>>>(x, y0, y1, n);
 }
 
 // Any alignment: one element per thread per iteration.
@@ -210,9 +341,9 @@ inline size_t grid_for(size_t units, size_t per_block, const LaunchCfg &c, int s
   return blocks;
 }
 
-template <typename T, class F, int D>
-ptrig_status launch_map_d(const LaunchCfg &c, int sms, const T *x, T *y0, T *y1, size_t n, cudaStream_t s) {
-  const size_t nvec = n / Storage<T>::EPV;
+template <typename T, class F, int D, int W>
+ptrig_status launch_map_w(const LaunchCfg &c, int sms, const T *x, T *y0, T *y1, size_t n, cudaStream_t s) {
+  const size_t nvec = n / (Storage<T>::EPV * W);  // groups of W vectors
   // one-shot needs one block per chunk; beyond the grid limit the persistent
   // grid (8 blocks per SM) walks the array instead
   const bool oneshot = c.blocks_per_sm == 0 && (nvec + (size_t)c.block * D - 1) / ((size_t)c.block * D) <= INT_MAX;
@@ -221,12 +352,24 @@ ptrig_status launch_map_d(const LaunchCfg &c, int sms, const T *x, T *y0, T *y1,
     const size_t cap = (size_t)sms * (size_t)(c.blocks_per_sm > 0 ? c.blocks_per_sm : 8);
     if (g > cap) g = cap;
     if (g < 1) g = 1;
-    launch_k_map<T, F, D, true>((unsigned)g, c.block, s, x, y0, y1, n);
-  } else {  // one-shot: one contiguous chunk of D * block vectors per block
+    launch_k_map<T, F, D, true, W>((unsigned)g, c.block, s, x, y0, y1, n);
+  } else {  // one-shot: one contiguous chunk of D * block groups per block
     const size_t g = grid_for(nvec, (size_t)c.block * D, LaunchCfg{c.block, D, 0}, sms);
-    launch_k_map<T, F, D, false>((unsigned)g, c.block, s, x, y0, y1, n);
+    launch_k_map<T, F, D, false, W>((unsigned)g, c.block, s, x, y0, y1, n);
   }
   return finish_launch();
+}
+
+// The functor's access width (F::GROUP 16-byte vectors per access) when every
+// pointer is aligned to it, 16-byte accesses otherwise.
+template <typename T, class F, int D>
+ptrig_status launch_map_d(const LaunchCfg &c, int sms, const T *x, T *y0, T *y1, size_t n, cudaStream_t s) {
+  if constexpr (F::GROUP == 2) {
+    uintptr_t a = (uintptr_t)x | (uintptr_t)y0;
+    if (F::NOUT == 2) a |= (uintptr_t)y1;
+    if ((a & 31u) == 0) return launch_map_w<T, F, D, 2>(c, sms, x, y0, y1, n, s);
+  }
+  return launch_map_w<T, F, D, 1>(c, sms, x, y0, y1, n, s);
 }
 
 template <typename T, class F>
