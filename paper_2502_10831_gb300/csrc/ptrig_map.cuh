@@ -2,9 +2,11 @@
 //
 // Reads use ld.global.nc.L1::no_allocate and writes st.global.cs: every byte is
 // touched once, so nothing is kept in L1 and the stores are marked
-// evict-first in L2.  The eight-entry coefficient
-// table is staged in shared memory; its 128 bytes occupy all 32 banks once,
-// so a warp's LDS.128 lookups never conflict.
+// evict-first in L2.  Kernels that use the eight-entry coefficient table stage
+// it in shared memory (its 128 bytes span the 32 banks once; a warp's LDS.128
+// lookups of up to eight rows take a few wavefronts at most) and move 16-byte
+// vectors; the table-free kernels (Taylor, CUDA's math functions) move 32-byte
+// groups when the pointers allow it.
 #pragma once
 
 #include <climits>
