@@ -50,9 +50,41 @@ __device__ __forceinline__ bool map_vector_fast_h(uint4 v, size_t i, T *y0, T *y
   return true;
 }
 
+// FP32 storage with the pair form: the four angles of a vector as two float2
+// pairs through the packed reduction and evaluation; the pair sign words hold
+// lane 0's sign at bit 15 and lane 1's at bit 31.
+template <class F>
+__device__ __forceinline__ bool map_vector_fast_f32pair(uint4 v, size_t i, float *y0, float *y1,
+                                                        const float4 *tab) {
+  const float f[4] = {__uint_as_float(v.x), __uint_as_float(v.y), __uint_as_float(v.z), __uint_as_float(v.w)};
+  bool slow = false;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) slow |= needs_slow(f[e]);
+  if (slow) return false;
+  uint32_t a[4], b[4];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    float2 m0, m1;
+    uint32_t s0, s1;
+    F::eval_pair_mag(make_float2(f[2 * k], f[2 * k + 1]), tab, m0, m1, s0, s1);
+    a[2 * k] = __float_as_uint(m0.x) ^ ((s0 << 16) & 0x80000000u);
+    a[2 * k + 1] = __float_as_uint(m0.y) ^ (s0 & 0x80000000u);
+    if constexpr (F::NOUT == 2) {
+      b[2 * k] = __float_as_uint(m1.x) ^ ((s1 << 16) & 0x80000000u);
+      b[2 * k + 1] = __float_as_uint(m1.y) ^ (s1 & 0x80000000u);
+    }
+  }
+  st_stream(reinterpret_cast<uint4 *>(y0) + i, make_uint4(a[0], a[1], a[2], a[3]));
+  if constexpr (F::NOUT == 2) st_stream(reinterpret_cast<uint4 *>(y1) + i, make_uint4(b[0], b[1], b[2], b[3]));
+  return true;
+}
+
 template <typename T, class F>
 __device__ __forceinline__ bool map_vector_fast(uint4 v, size_t i, T *y0, T *y1, const float4 *tab) {
   if constexpr (F::HAS_PAIR && sizeof(T) == 2) return map_vector_fast_h<T, F>(v, i, y0, y1, tab);
+  if constexpr (F::HAS_PAIR && sizeof(T) == 4) {
+    if constexpr (F::PAIR_F32) return map_vector_fast_f32pair<F>(v, i, y0, y1, tab);
+  }
   using S = Storage<T>;
   constexpr int E = S::EPV;
   float f[E], o0[E], o1[E];
