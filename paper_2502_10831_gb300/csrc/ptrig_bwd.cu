@@ -165,10 +165,15 @@ ptrig_status launch_bwd_f32(int op, const float *x, const float *gy, float *gx, 
 
 // One pass of  L = sum_i w_i sin(x_i) + v_i cos(x_i) + u_i clamp(tan(x_i), lo, hi)
 // and dL/dx_i with the paper's functions: one reduction and one table lookup
-// give N, D, rs = 1/h and rd = 1/D; then
-//   sin = N rs, cos = D rs, tan = N rd               (signed as in sign_bits)
-//   dsin = D Dl rs^3, dcos = -N Dl rs^3, dtan = Dl rd^2  (times s_f sign(r))
-// and the clamp passes the gradient where lo <= tan <= hi.
+// give N, D, rs = 1/h and rd = 1/D.  With s_f the sign of function f and
+// s_r the sign of r, and the weights carrying the function signs
+// (ws = s_sin w, vc = s_cos v, ut = s_tan u):
+//   w sin + v cos = rs (ws N + vc D),     tan = s_tan N rd
+//   dL/dx = s_r Dl [ rs^3 (ws D - vc N) + [lo <= tan <= hi] ut rd^2 ]
+// which is w dsin + v dcos + u dtan with dsin = s_sin s_r D Dl rs^3,
+// dcos = -s_cos s_r N Dl rs^3, dtan = s_tan s_r Dl rd^2 (Dl = aN bD - bN aD of
+// the row, the derivative of N / D in t), regrouped so that the signs are
+// applied once to the weights.
 template <bool FULL>
 __device__ __forceinline__ float loss_element(float x, float w, float v, float u, float lo, float hi,
                                               const float4 *tab, float &g) {
@@ -182,17 +187,16 @@ __device__ __forceinline__ float loss_element(float x, float w, float v, float u
   const uint32_t sr = __float_as_uint(red.r) & 0x80000000u;
   const float rs = rsqrt_approx(__fmaf_rn(N, N, __fmul_rn(D, D)));
   const float rd = rcp_approx(D);
-  const float rs3 = __fmul_rn(rs, __fmul_rn(rs, rs));
-  const float sv = xor_sign(__fmul_rn(N, rs), sg.s);
-  const float cv = xor_sign(__fmul_rn(D, rs), sg.c);
+  const float ws = xor_sign(w, sg.s);
+  const float vc = xor_sign(v, sg.c);
   const float tv = xor_sign(__fmul_rn(N, rd), sg.t);
-  const float ds = xor_sign(__fmul_rn(__fmul_rn(D, dl), rs3), sg.s ^ sr);
-  const float dc = xor_sign(__fmul_rn(__fmul_rn(-N, dl), rs3), sg.c ^ sr);
-  const float dt = xor_sign(__fmul_rn(dl, __fmul_rn(rd, rd)), sg.t ^ sr);
   const bool inside = (tv >= lo) && (tv <= hi);
   const float tc = fminf(fmaxf(tv, lo), hi);
-  g = __fmaf_rn(w, ds, __fmaf_rn(v, dc, inside ? __fmul_rn(u, dt) : 0.0f));
-  return __fmaf_rn(w, sv, __fmaf_rn(v, cv, __fmul_rn(u, tc)));
+  const float rs3 = __fmul_rn(rs, __fmul_rn(rs, rs));
+  const float sc = __fmul_rn(__fmaf_rn(ws, D, -__fmul_rn(vc, N)), rs3);
+  const float ut = inside ? xor_sign(u, sg.t) : 0.0f;
+  g = xor_sign(__fmul_rn(dl, __fmaf_rn(ut, __fmul_rn(rd, rd), sc)), sr);
+  return __fmaf_rn(rs, __fmaf_rn(ws, N, __fmul_rn(vc, D)), __fmul_rn(u, tc));
 }
 
 struct LossVec {
