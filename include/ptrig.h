@@ -206,19 +206,20 @@ typedef enum ptrig_family {
   PTRIG_FAMILY_COUNT = 9
 } ptrig_family;
 
-/* Threads per block (64..512, multiple of 32), 16-byte loads kept in flight
- * per thread (1, 2, 4, or 8 for fp16 / bf16; 8 acts as 4 for 4-byte types)
- * and the grid shape: blocks_per_sm = 0 launches one
- * block per contiguous chunk of block * vec_per_thread vectors (one-shot);
- * blocks_per_sm = k > 0 launches a persistent grid of k blocks per SM that
- * strides over the array.  Process-wide; affects later launches.  The
- * defaults were measured on GB300. */
+/* Threads per block (64..512, multiple of 32), loads kept in flight per
+ * thread (1, 2, 4, or 8 for fp16 / bf16; 8 acts as 4 for 4-byte types) and
+ * the grid shape: blocks_per_sm = 0 launches one block per contiguous chunk
+ * of block * vec_per_thread loads (one-shot); blocks_per_sm = k > 0 launches
+ * a persistent grid of k blocks per SM that strides over the array.  A load
+ * is 16 bytes, or 32 bytes for the Taylor and CUDA-math families when every
+ * pointer of the call is 32-byte aligned.  Process-wide; affects later
+ * launches.  The defaults were measured on GB300. */
 ptrig_status ptrig_set_launch_config(int family, int block, int vec_per_thread, int blocks_per_sm);
 ptrig_status ptrig_get_launch_config(int family, int *block, int *vec_per_thread, int *blocks_per_sm);
 
 /* ------------------------------------------------------------------------ */
 /* Ragged batch: many arrays with per-array function selectors in ONE      */
-/* persistent launch                                                        */
+/* kernel launch                                                            */
 /* ------------------------------------------------------------------------ */
 
 /* One array of the batch.  x: n device floats; y0: n device floats (sin,
