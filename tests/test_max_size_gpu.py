@@ -87,3 +87,33 @@ def _segments(B, xs):
     B.ptrig_segment_f32(xt, s)
     torch.cuda.synchronize()
     return s.cpu().numpy()
+
+
+def test_batch_array_past_2_pow_31(B, oracle):
+    """A ragged batch whose first array has 2^31 + 77 elements (tile offsets
+    past 2^31) next to two small arrays, as one graph launch."""
+    n_big = (1 << 31) + 77
+    x = _device_uniform(n_big, 73)
+    ys = torch.empty_like(x)
+    yc = torch.empty_like(x)
+    xs_small = _device_uniform(1000, 74)
+    ya = torch.empty_like(xs_small)
+    yb = torch.empty_like(xs_small)
+    descs = [(x, ys, yc, n_big, B.SINCOS), (xs_small, ya, None, 1000, B.SIN), (xs_small[3:], yb[3:], None, 997, B.TAN)]
+    plan = B.BatchPlan(descs, B.BATCH_GRAPH)
+    plan.run()
+    torch.cuda.synchronize()
+    idx = torch.from_numpy(_positions(n_big, 8)).cuda()
+    xv = x[idx].cpu().numpy()
+    xd = xv.astype(np.float64)
+    for name, t in (("sin", ys), ("cos", yc)):
+        ref, _ = P.reference_with_gpu_segments(oracle, name, xd, _segments(B, xv))
+        P.check_values(oracle, name, xd, t[idx].cpu().numpy(), ref)
+    xsd = xs_small.cpu().numpy()
+    ref, _ = P.reference_with_gpu_segments(oracle, "sin", xsd.astype(np.float64), _segments(B, xsd))
+    P.check_values(oracle, "sin", xsd.astype(np.float64), ya.cpu().numpy(), ref)
+    ref, _ = P.reference_with_gpu_segments(oracle, "tan", xsd[3:].astype(np.float64), _segments(B, xsd[3:]))
+    P.check_values(oracle, "tan", xsd[3:].astype(np.float64), yb[3:].cpu().numpy(), ref)
+    plan.close()
+    del x, ys, yc
+    torch.cuda.empty_cache()
