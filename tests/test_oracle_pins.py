@@ -405,6 +405,26 @@ def test_taylor5_sup_errors_consistent_with_tables(oracle):
     assert 2.4e-5 <= ec < 2.5e-5 and GOLDEN["table2_cos"]["taylor5_simd"]["abs_max"] <= ec
 
 
+def test_taylor_n_sup_errors_on_the_reduced_range(oracle):
+    """On [0, pi/2] the n-term Maclaurin polynomials of sin and cos err most
+    at u = pi/2, where the alternating series' truncation error is largest:
+    T5 3.54e-6 / 2.47e-5, T7 6.6e-10 / 6.3e-9, T9 4.4e-14 / 5.3e-13 (sin / cos).
+    Checked on a dense grid and, at pi/2, against the first omitted term as an
+    upper bound (alternating series with decreasing terms there)."""
+    u = np.linspace(0, HALF_PI, 200_001)
+    expect = {5: (3.54e-6, 2.47e-5), 7: (6.6e-10, 6.3e-9), 9: (4.4e-14, 5.3e-13)}
+    for n, (e_sin, e_cos) in expect.items():
+        es = np.abs(oracle.taylor(0, n, u) - np.sin(u))
+        ec = np.abs(oracle.taylor(1, n, u) - np.cos(u))
+        # FP64 rounding (a few 1e-16) blurs the 4.4e-14 of T9: looser value, argmax near pi/2
+        tol, near = (0.02, 2) if n < 9 else (0.1, 100)
+        assert es.max() == pytest.approx(e_sin, rel=tol) and int(np.argmax(es)) >= u.size - near, n
+        assert ec.max() == pytest.approx(e_cos, rel=tol) and int(np.argmax(ec)) >= u.size - near, n
+        first_omitted_sin = HALF_PI ** (2 * n + 1) / math.factorial(2 * n + 1)
+        first_omitted_cos = HALF_PI ** (2 * n) / math.factorial(2 * n)
+        assert es[-1] <= first_omitted_sin and ec[-1] <= first_omitted_cos, n
+
+
 def test_taylor_tan_table3_single_angle(oracle):
     """Table 3's Taylor-5/7/9 maxima come from one angle with tan ~ 160: solving
     the Taylor-5 column for that angle reproduces the Taylor-7 column and all
@@ -443,3 +463,25 @@ def test_derivative_closed_form_at_zero(oracle):
     assert float(oracle.derivative(0, z)[0]) == pytest.approx(v, rel=1e-14)
     assert float(oracle.derivative(2, z)[0]) == pytest.approx(v, rel=1e-14)
     assert float(oracle.derivative(1, z)[0]) == pytest.approx(0.0, abs=1e-15)
+
+
+def test_derivative_per_segment_constants(oracle):
+    """Per segment the derivative of tan = N / D in u is R dA / D^2, with the
+    integers dA = A D - B C of the appendix quadruples (6952, 6610, 3476,
+    15341, 6610, 6952 in degrees), and d sin / du = R dA D / h^3,
+    d cos / du = -R dA N / h^3 (h^2 = N^2 + D^2).  Checked at the middle of
+    each segment, in the first quadrant."""
+    dA = [6952, 6610, 3476, 15341, 6610, 6952]
+    quads = [(11, 0, -1, 632), (10, 10, -4, 657), (6, 46, -5, 541), (10, 217, -13, 1252), (4, 297, -10, 910),
+             (1, 542, -11, 990)]
+    R = 180.0 / PI
+    for k, ((A, B_, C, D), d) in enumerate(zip(quads, dA)):
+        assert A * D - B_ * C == d
+        u = (k + 0.5) * PI / 12
+        N = A * R * u + B_
+        Dn = C * R * u + D
+        h3 = (N * N + Dn * Dn) ** 1.5
+        x = np.array([u])
+        assert float(oracle.derivative(2, x)[0]) == pytest.approx(R * d / Dn ** 2, rel=1e-12), k
+        assert float(oracle.derivative(0, x)[0]) == pytest.approx(R * d * Dn / h3, rel=1e-12), k
+        assert float(oracle.derivative(1, x)[0]) == pytest.approx(-R * d * N / h3, rel=1e-12), k
