@@ -42,6 +42,9 @@ MUTATIONS = {
     "faithful_selector": ("int k = (int)floor(u / 0.261);\n  if (k > 5) k = 5;",
                           "int k = (int)floor(u / 0.2618);\n  if (k > 5) k = 5;"),
     "faithful_newton": ("y = y * (1.5 - (v * 0.5) * y * y);", "y = y * (1.5 - (v * 0.25) * y * y);"),
+    "neighbour_direction": ("  int k = segment(r.u) + dk;\n", "  int k = segment(r.u) - dk;\n"),
+    "neighbour_ignores_shift": ("  int k = segment(r.u) + dk;\n", "  int k = segment(r.u) + 0 * dk;\n"),
+    "neighbour_clamp": ("  int k = segment(r.u) + dk;\n  if (k < 0) k = 0;", "  int k = segment(r.u) + dk;\n  if (k < 0) k = 1;"),
 }
 
 PIN_TESTS = [getattr(pins, n) for n in dir(pins) if n.startswith("test_")]

@@ -217,6 +217,41 @@ def test_node_values_are_exact_rationals(oracle):
     assert float(oracle.proposed(1, np.array([HALF_PI]))[0]) == pytest.approx(0.0, abs=1e-13)
 
 
+def test_neighbour_segment_is_the_adjacent_formula(oracle):
+    """proposed_neighbour(f, dk, x) evaluates segment k + dk's formula at x's
+    reduced angle: just right of node m (segment m) with dk = -1 it gives
+    segment m-1's exact node rational, just left of it (segment m-1) with
+    dk = +1 segment m's -- in all four quadrants and for negative x, with the
+    quadrant signs of the function itself; shifts that leave 0..5 are clamped."""
+    eps = 1e-12
+    for m in range(1, 6):
+        for side, dk, key in ((1, -1, (m - 1, m)), (-1, 1, (m, m))):
+            t = float(NODE_TAN[key])
+            c0 = 1.0 / math.sqrt(1.0 + t * t)
+            for q in range(4):
+                u = m * PI / 12 + side * eps
+                rho = u if q % 2 == 0 else HALF_PI - u
+                for sg in (1.0, -1.0):
+                    x = np.array([sg * (q * HALF_PI + rho)])
+                    want = {
+                        0: sg * (1 if q in (0, 1) else -1) * t * c0,
+                        1: (1 if q in (0, 3) else -1) * c0,
+                        2: sg * (1 if q % 2 == 0 else -1) * t,
+                    }
+                    for f, w in want.items():
+                        got = float(oracle.proposed_neighbour(f, dk, x)[0])
+                        assert got == pytest.approx(w, rel=1e-9, abs=1e-10), (m, side, q, sg, f)
+    # clamping: no segment below 0 or above 5
+    for u, dk in ((0.1, -1), (1.5, 1), (0.1, -3), (1.5, 4)):
+        x = np.array([u, HALF_PI + (HALF_PI - u), -u])
+        for f in (0, 1, 2):
+            assert np.array_equal(oracle.proposed_neighbour(f, dk, x), oracle.proposed(f, x)), (u, dk, f)
+    # dk = 0 is the function itself
+    x = np.random.default_rng(5).uniform(-20, 20, 1000)
+    for f in (0, 1, 2):
+        assert np.array_equal(oracle.proposed_neighbour(f, 0, x), oracle.proposed(f, x))
+
+
 def test_jumps_at_nodes(oracle):
     """Rounding the rationals to integers makes tan jump at 15, 30, 60, 75 degrees
     (by the exact differences of the rationals) and not at 45 degrees."""
