@@ -83,7 +83,9 @@ def f64(v: Fraction, mode: str = "nearest") -> float:
 
 
 def lit32(x: float) -> str:
-    return "0.0f" if x == 0 else f"{x.hex()}f"
+    if x == 0:
+        return "-0.0f" if math.copysign(1.0, x) < 0 else "0.0f"
+    return f"{x.hex()}f"
 
 
 def lit64(x: float) -> str:
@@ -121,6 +123,12 @@ def main() -> str:
     w(f"#define PTRIG_RINT_MAGIC_F {lit32(1.5 * 2.0 ** 23)}")
     w("/* FP32 reduction bound 2^20 (FP64 Cody-Waite or Payne-Hanek above) */")
     w(f"#define PTRIG_FAST_LIMIT_F {lit32(2.0 ** 20)}")
+    w("/* FP32 reduction bound of the signed-row kernels: M + 8 j stays exact")
+    w(" * in [2^23, 2^24) for |j| <= 2^19 * 2/pi + 1 < 2^19 */")
+    w(f"#define PTRIG_SEG_LIMIT_F {lit32(2.0 ** 19)}")
+    w("/* bits of 1.5 * 2^23, and -7 * 1.5 * 2^23: fma(8, M + j, -7 M) = M + 8 j exactly */")
+    w("#define PTRIG_RINT_MAGIC_BITS 0x4b400000u")
+    w(f"#define PTRIG_SEG_BASE_C {lit32(-7 * 1.5 * 2.0 ** 23)}")
     w("")
 
     # ---- FP64 Cody-Waite (|j| < 2^31)
@@ -182,6 +190,41 @@ def main() -> str:
     for i, (aN, bN, aD, bD, k) in enumerate(rows):
         sep = "," if i < 7 else ""
         w(f"  {lit64(f64(aN))}, {lit64(f64(bN))}, {lit64(f64(aD))}, {lit64(f64(bD))}{sep} /* seg {k} */ \\")
+    w("")
+
+    # ---- signed rows: the same formulas in the signed r, indexed by
+    # i = (8 j + f) mod 16 with f = floor(r 12/pi) in [-4, 3].  j' = j - [r < 0]
+    # (the quadrant below x) has j' & 1 = bit 3 of i; f' = i & 7 is f for r >= 0
+    # (kq = f') and f + 8 for r < 0 (kq = 7 - f', and j = j' + 1).  In every row
+    # N >= 0 and D carries the sign (-1)^(j' & 1); sin and cos take the further
+    # sign (-1)^((j' >> 1) & 1) from bit 4 of (8 j + f), tan none.
+    srows = []
+    for i in range(16):
+        jp, fp = i >> 3, i & 7
+        if fp <= 3:
+            kq, p, sr = fp, jp, 0
+        else:
+            kq, p, sr = 7 - fp, 1 - jp, 1
+        aN, bN, aD, bD, k = rows[(p << 2) | kq]
+        if sr:  # t = -r
+            aN, aD = -aN, -aD
+        if jp:
+            aD, bD = -aD, -bD
+        srows.append((aN, bN, aD, bD, k, jp, sr))
+    w("/* Signed rows: index i = (8 j + f) mod 16, f = floor(r 12/pi) in [-4, 3];")
+    w(" * N = aN r + bN >= 0, D = aD r + bD with the sign of (j - [r < 0]) & 1")
+    w(" * folded in; A holds {aN, aD}, B {bN, bD}.  Row 0's bN is -0 so that")
+    w(" * x = -0 gives N = -0. */")
+    w("#define PTRIG_SROW_A_F32 \\")
+    for i, (aN, bN, aD, bD, k, jp, sr) in enumerate(srows):
+        sep = "," if i < 15 else ""
+        w(f"  {{{lit32(f32(aN))}, {lit32(f32(aD))}}}{sep} /* {i}: seg {k}, j' odd {jp}, r<0 {sr} */ \\")
+    w("")
+    w("#define PTRIG_SROW_B_F32 \\")
+    for i, (aN, bN, aD, bD, k, jp, sr) in enumerate(srows):
+        sep = "," if i < 15 else ""
+        bn = -0.0 if i == 0 else f32(bN)
+        w(f"  {{{lit32(bn)}, {lit32(f32(bD))}}}{sep} \\")
     w("")
 
     # ---- u-form FP64 coefficients for the paper-faithful kernels

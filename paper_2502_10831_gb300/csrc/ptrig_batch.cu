@@ -56,10 +56,11 @@ namespace ptrig {
 static_assert(sizeof(ptrig_desc) == 40, "ptrig_desc layout");
 
 // Vectors v, v + blockDim, ... < nv of one tile with the full reduction (out
-// of line; reached only when the tile holds an angle beyond 2^20).
+// of line; reached only when the tile holds an angle beyond the FP32
+// reduction range).
 template <int OP>
 static __device__ __noinline__ void batch_resume_full(const float *x, float *y0, float *y1, uint32_t v,
-                                                      uint32_t nv, const float4 *tab) {
+                                                      uint32_t nv, const STab *tab) {
   using F = Proposed<OP>;
   for (; v < nv; v += blockDim.x) {
     float f[4], o0[4], o1[4];
@@ -74,7 +75,7 @@ static __device__ __noinline__ void batch_resume_full(const float *x, float *y0,
 // out of line like the full-reduction path.
 template <int OP>
 static __device__ __noinline__ void batch_elements(const float *x, float *y0, float *y1, uint32_t from,
-                                                   uint32_t len, const float4 *tab) {
+                                                   uint32_t len, const STab *tab) {
   using F = Proposed<OP>;
   for (uint32_t i = from + threadIdx.x; i < len; i += blockDim.x) {
     float o0, o1;
@@ -90,7 +91,7 @@ static __device__ __noinline__ void batch_elements(const float *x, float *y0, fl
 // n % 4 tail.
 template <int OP>
 static __device__ __noinline__ void batch_tile(const ptrig_desc d, uint64_t start, uint32_t len,
-                                               const float4 *tab) {
+                                               const STab *tab) {
   using F = Proposed<OP>;
   const float *x = d.x + start;
   float *y0 = d.y0 + start;
@@ -139,9 +140,9 @@ static __device__ __noinline__ void batch_tile(const ptrig_desc d, uint64_t star
 // are 16-byte aligned (a ring of four 16-byte loads per thread, the next load
 // of a slot issued before the slot's vector is computed); element path
 // otherwise and for the len % 4 tail; out-of-line full reduction after an
-// angle beyond 2^20, as in the elementwise kernels.
+// angle beyond the FP32 reduction range, as in the elementwise kernels.
 template <int OP>
-__device__ __forceinline__ void batch_block(const BatchTile &t, const float4 *s_tab) {
+__device__ __forceinline__ void batch_block(const BatchTile &t, const STab *s_tab) {
   using F = Proposed<OP>;
   float *y1 = (OP == OP_SINCOS) ? t.y1 : nullptr;
   uintptr_t a = (uintptr_t)t.x | (uintptr_t)t.y0;
@@ -183,19 +184,19 @@ tail:
 // holds b -- uniform over the block, so the branch never diverges.
 __global__ void __launch_bounds__(512) k_batch_tiles(const BatchTile *__restrict__ tiles, uint32_t end_sin,
                                                      uint32_t end_cos, uint32_t end_tan) {
-  __shared__ float4 s_tab[8];
-  if (threadIdx.x < 8) s_tab[threadIdx.x] = c_tab_f32[threadIdx.x];
+  __shared__ STab s_tab;
+  stage_stab(&s_tab);
   const uint32_t b = blockIdx.x;
   const BatchTile t = tiles[b];
   __syncthreads();
   if (b < end_sin)
-    batch_block<OP_SIN>(t, s_tab);
+    batch_block<OP_SIN>(t, &s_tab);
   else if (b < end_cos)
-    batch_block<OP_COS>(t, s_tab);
+    batch_block<OP_COS>(t, &s_tab);
   else if (b < end_tan)
-    batch_block<OP_TAN>(t, s_tab);
+    batch_block<OP_TAN>(t, &s_tab);
   else
-    batch_block<OP_SINCOS>(t, s_tab);
+    batch_block<OP_SINCOS>(t, &s_tab);
 }
 
 // ---------------------------------------------------------------------------
@@ -257,8 +258,8 @@ __global__ void __launch_bounds__(1024) k_noalloc_prefix(const ptrig_desc *__res
 __global__ void __launch_bounds__(512, 2) k_batch_noalloc(const ptrig_desc *__restrict__ descs, uint32_t count,
                                                           const uint64_t *__restrict__ first_tile,
                                                           uint32_t tile_elems) {
-  __shared__ float4 s_tab[8];
-  if (threadIdx.x < 8) s_tab[threadIdx.x] = c_tab_f32[threadIdx.x];
+  __shared__ STab s_tab;
+  stage_stab(&s_tab);
   __syncthreads();
   const uint64_t ntiles = first_tile[count];
   for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -276,16 +277,16 @@ __global__ void __launch_bounds__(512, 2) k_batch_noalloc(const ptrig_desc *__re
     const uint32_t len = rem < tile_elems ? (uint32_t)rem : tile_elems;
     switch (d.func) {
       case PTRIG_SIN:
-        batch_tile<OP_SIN>(d, start, len, s_tab);
+        batch_tile<OP_SIN>(d, start, len, &s_tab);
         break;
       case PTRIG_COS:
-        batch_tile<OP_COS>(d, start, len, s_tab);
+        batch_tile<OP_COS>(d, start, len, &s_tab);
         break;
       case PTRIG_TAN:
-        batch_tile<OP_TAN>(d, start, len, s_tab);
+        batch_tile<OP_TAN>(d, start, len, &s_tab);
         break;
       default:
-        batch_tile<OP_SINCOS>(d, start, len, s_tab);
+        batch_tile<OP_SINCOS>(d, start, len, &s_tab);
         break;
     }
   }

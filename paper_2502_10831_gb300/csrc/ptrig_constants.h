@@ -14,6 +14,12 @@
 #define PTRIG_RINT_MAGIC_F 0x1.8000000000000p+23f
 /* FP32 reduction bound 2^20 (FP64 Cody-Waite or Payne-Hanek above) */
 #define PTRIG_FAST_LIMIT_F 0x1.0000000000000p+20f
+/* FP32 reduction bound of the signed-row kernels: M + 8 j stays exact
+ * in [2^23, 2^24) for |j| <= 2^19 * 2/pi + 1 < 2^19 */
+#define PTRIG_SEG_LIMIT_F 0x1.0000000000000p+19f
+/* bits of 1.5 * 2^23, and -7 * 1.5 * 2^23: fma(8, M + j, -7 M) = M + 8 j exactly */
+#define PTRIG_RINT_MAGIC_BITS 0x4b400000u
+#define PTRIG_SEG_BASE_C -0x1.5000000000000p+26f
 
 /* pi/2 = PIO2_D1 + PIO2_D2 + PIO2_D3 (+ ~2^-127): 21 + 53 + 53 bits */
 #define PTRIG_PIO2_D1 0x1.921fb00000000p+0
@@ -62,6 +68,46 @@
   -0x1.ca5dc1a63c1f8p+7, 0x1.4880000000000p+9, 0x1.1e7a9907e593bp+9, 0x1.4000000000000p+3, /* seg 4 */ \
   -0x1.1e7a9907e593bp+9, 0x1.1740000000000p+10, 0x1.746c2d5710d99p+9, 0x1.4800000000000p+6, /* seg 3 */ \
   -0x1.57c6513cad17ap+8, 0x1.2500000000000p+9, 0x1.1e7a9907e593bp+8, 0x1.6c00000000000p+6 /* seg 2 */ \
+
+/* Signed rows: index i = (8 j + f) mod 16, f = floor(r 12/pi) in [-4, 3];
+ * N = aN r + bN >= 0, D = aD r + bD with the sign of (j - [r < 0]) & 1
+ * folded in; A holds {aN, aD}, B {bN, bD}.  Row 0's bN is -0 so that
+ * x = -0 gives N = -0. */
+#define PTRIG_SROW_A_F32 \
+  {0x1.3b20760000000p+9f, -0x1.ca5dc20000000p+5f}, /* 0: seg 0, j' odd 0, r<0 0 */ \
+  {0x1.1e7a9a0000000p+9f, -0x1.ca5dc20000000p+7f}, /* 1: seg 1, j' odd 0, r<0 0 */ \
+  {0x1.57c6520000000p+8f, -0x1.1e7a9a0000000p+8f}, /* 2: seg 2, j' odd 0, r<0 0 */ \
+  {0x1.1e7a9a0000000p+9f, -0x1.746c2e0000000p+9f}, /* 3: seg 3, j' odd 0, r<0 0 */ \
+  {0x1.57c6520000000p+8f, -0x1.1e7a9a0000000p+8f}, /* 4: seg 2, j' odd 0, r<0 1 */ \
+  {0x1.1e7a9a0000000p+9f, -0x1.746c2e0000000p+9f}, /* 5: seg 3, j' odd 0, r<0 1 */ \
+  {0x1.ca5dc20000000p+7f, -0x1.1e7a9a0000000p+9f}, /* 6: seg 4, j' odd 0, r<0 1 */ \
+  {0x1.ca5dc20000000p+5f, -0x1.3b20760000000p+9f}, /* 7: seg 5, j' odd 0, r<0 1 */ \
+  {-0x1.ca5dc20000000p+5f, -0x1.3b20760000000p+9f}, /* 8: seg 5, j' odd 1, r<0 0 */ \
+  {-0x1.ca5dc20000000p+7f, -0x1.1e7a9a0000000p+9f}, /* 9: seg 4, j' odd 1, r<0 0 */ \
+  {-0x1.1e7a9a0000000p+9f, -0x1.746c2e0000000p+9f}, /* 10: seg 3, j' odd 1, r<0 0 */ \
+  {-0x1.57c6520000000p+8f, -0x1.1e7a9a0000000p+8f}, /* 11: seg 2, j' odd 1, r<0 0 */ \
+  {-0x1.1e7a9a0000000p+9f, -0x1.746c2e0000000p+9f}, /* 12: seg 3, j' odd 1, r<0 1 */ \
+  {-0x1.57c6520000000p+8f, -0x1.1e7a9a0000000p+8f}, /* 13: seg 2, j' odd 1, r<0 1 */ \
+  {-0x1.1e7a9a0000000p+9f, -0x1.ca5dc20000000p+7f}, /* 14: seg 1, j' odd 1, r<0 1 */ \
+  {-0x1.3b20760000000p+9f, -0x1.ca5dc20000000p+5f} /* 15: seg 0, j' odd 1, r<0 1 */ \
+
+#define PTRIG_SROW_B_F32 \
+  {-0.0f, 0x1.3c00000000000p+9f}, \
+  {0x1.4000000000000p+3f, 0x1.4880000000000p+9f}, \
+  {0x1.7000000000000p+5f, 0x1.0e80000000000p+9f}, \
+  {0x1.b200000000000p+7f, 0x1.3900000000000p+10f}, \
+  {0x1.2500000000000p+9f, 0x1.6c00000000000p+6f}, \
+  {0x1.1740000000000p+10f, 0x1.4800000000000p+6f}, \
+  {0x1.4880000000000p+9f, 0x1.4000000000000p+3f}, \
+  {0x1.3c00000000000p+9f, 0.0f}, \
+  {0x1.3c00000000000p+9f, 0.0f}, \
+  {0x1.4880000000000p+9f, -0x1.4000000000000p+3f}, \
+  {0x1.1740000000000p+10f, -0x1.4800000000000p+6f}, \
+  {0x1.2500000000000p+9f, -0x1.6c00000000000p+6f}, \
+  {0x1.b200000000000p+7f, -0x1.3900000000000p+10f}, \
+  {0x1.7000000000000p+5f, -0x1.0e80000000000p+9f}, \
+  {0x1.4000000000000p+3f, -0x1.4880000000000p+9f}, \
+  {0.0f, -0x1.3c00000000000p+9f} \
 
 /* Sec. 2 formulas in the paper's variable u for segments 0..5:
  * {a, b, c, d} = {A R, B, C R, D}, then the sin/cos radicand coefficients

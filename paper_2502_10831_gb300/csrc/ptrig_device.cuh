@@ -5,17 +5,18 @@
 //   1. reduction  x = j pi/2 + r with |r| <~ pi/4 (Sec. 3 reduces to [0, pi/2]
 //      with a sign; here the nearest multiple of pi/2 is taken and the paper's
 //      angle is u = t for even j, u = pi/2 - t for odd j, t = |r|):
-//        |x| <= 2^20    : FP32 Cody-Waite with FMA, 24+24+24-bit split of pi/2
+//        |x| <= 2^19    : FP32 Cody-Waite with FMA, 24+24+24-bit split of pi/2
+//                         (2^20 in the derivative kernels)
 //        |x| <  2^31    : FP64 Cody-Waite, 21+53+53-bit split
 //        otherwise      : Payne-Hanek, exact integer product with 2/pi
-//   2. segment  kq = floor(t 12/pi) in 0..3; segment k = kq (even j) or
-//      5 - kq (odd j), the Sec. 2 domains [k pi/12, (k+1) pi/12).
-//   3. evaluate  N = aN t + bN, D = aD t + bD from the 8-entry table indexed by
-//      (j & 1, kq): the Sec. 2 numerator and denominator of segment k written
-//      in t (the odd-j rows substitute u = pi/2 - t, which keeps D exactly
-//      proportional to t at the pole).  tan = N/D, sin = N/h, cos = D/h with
-//      h = sqrt(N^2 + D^2) (appendix A.4).
-//   4. sign  from j mod 4 and the sign of r (see sign_bits()).
+//   2. segment  f = floor(r 12/pi) in [-4, 3] from one FMA rounded down onto
+//      M + 8 j; the low four bits of the result, (8 j + f) mod 16, index a
+//      16-row table of the Sec. 2 formulas written in the signed r (segment
+//      kq or 5 - kq of the paper's u, kq = floor(|r| 12/pi)), and bit 4 is
+//      the sign of sin and cos in quadrants 2 and 3.
+//   3. evaluate  N = aN r + bN >= 0 and D = aD r + bD (its sign folded into
+//      the row): tan = N/D, sin = N/h, cos = D/h with h = sqrt(N^2 + D^2)
+//      (appendix A.4); sin and cos then take the quadrant sign.
 #pragma once
 
 #include <cstdint>
@@ -29,8 +30,24 @@ namespace ptrig {
 
 enum Op : int { OP_SIN = 0, OP_COS = 1, OP_TAN = 2, OP_SINCOS = 3 };
 
-// Coefficient table {aN, bN, aD, bD}, index (p << 2) | kq (see ptrig_constants.h).
+// Coefficient table {aN, bN, aD, bD}, index (p << 2) | kq (see ptrig_constants.h),
+// used by the derivative kernels.
 static __constant__ float4 c_tab_f32[8] = {PTRIG_TABLE_F32};
+
+// Signed rows of the forward kernels (see ptrig_constants.h): a[i] = {aN, aD},
+// b[i] = {bN, bD}.  Each half is 128 bytes, so a warp's 8-byte lookups from
+// shared memory never conflict (a half-warp touches each bank once at most).
+struct STab {
+  float2 a[16];
+  float2 b[16];
+};
+static __constant__ STab c_stab = {{PTRIG_SROW_A_F32}, {PTRIG_SROW_B_F32}};
+
+// Copies the signed rows into a block's shared-memory table (caller syncs).
+__device__ __forceinline__ void stage_stab(STab *s) {
+  for (int k = threadIdx.x; k < 16; k += blockDim.x)
+    reinterpret_cast<float4 *>(s)[k] = reinterpret_cast<const float4 *>(&c_stab)[k];
+}
 static __constant__ double c_tab_f64[32] = {PTRIG_TABLE_F64};
 static __constant__ uint32_t c_two_over_pi[PTRIG_TWO_OVER_PI_NWORDS] = {PTRIG_TWO_OVER_PI_WORDS};
 
@@ -212,17 +229,19 @@ __device__ __forceinline__ double reduce_d(double x, uint32_t *jb) {
   return reduce_payne_hanek(x, jb);
 }
 
-// Side path for FP32 inputs with |x| > 2^20, infinities and NaN.
+// Side path for FP32 inputs beyond the FP32 reduction range, infinities and
+// NaN.  jb holds the bits of the float M + (j mod 4), M = 1.5 * 2^23, as the
+// FP32 reduction's y = M + j does: the low bits are j mod 4 either way.
 static __device__ __noinline__ RedF reduce_slow_f32(float x) {
-  if (!isfinite(x)) return {__int_as_float(0x7fffffff), 0u};
+  if (!isfinite(x)) return {__int_as_float(0x7fffffff), PTRIG_RINT_MAGIC_BITS};
   uint32_t jb;
   const double r = reduce_d((double)x, &jb);
-  return {__double2float_rn(r), jb};
+  return {__double2float_rn(r), PTRIG_RINT_MAGIC_BITS | (jb & 3u)};
 }
 
-__device__ __forceinline__ RedF reduce_f32(float x) {
+__device__ __forceinline__ RedF reduce_f32(float x, float lim = PTRIG_FAST_LIMIT_F) {
   RedF red = reduce_fast(x);
-  if (__builtin_expect(!(fabsf(x) <= PTRIG_FAST_LIMIT_F), 0)) red = reduce_slow_f32(x);
+  if (__builtin_expect(!(fabsf(x) <= lim), 0)) red = reduce_slow_f32(x);
   return red;
 }
 
@@ -267,57 +286,91 @@ __device__ __forceinline__ uint32_t table_index(float t, uint32_t jb) {
   return ((jb & 1u) << 2) | segment_kq(t);
 }
 
-// Pair form for 16-bit storage: magnitudes m0 (and m1 for sincos), all >= 0,
-// and one sign word per output whose bits 15 and 31 are the signs of lanes 0
-// and 1 -- the sign positions of a packed half2 / bfloat162 word, so that one
-// XOR signs both lanes after rounding (round-to-nearest is sign-symmetric, so
-// this equals rounding the signed value).  The lanes' j and r sign bits are
-// gathered into one word with byte permutes before the sign_bits() logic:
-//   J = {.., jb0.byte0, .., jb1.byte0}: p at bits 8 / 24, j1 at bits 9 / 25
-//   R = {.., r0.byte3, .., r1.byte3}:   sr at bits 15 / 31
+// ------------------------------------------------- signed rows (forward)
+
+// The row code of the signed-row table.  With y = M + j from the FP32
+// reduction (M = 1.5 * 2^23; the side path supplies M + (j mod 4), which has
+// the same low bits), c = fma(8, y, -7 M) = M + 8 j exactly for |j| < 2^19,
+// and one FMA rounded toward -inf gives M + 8 j + floor(r RN(12/pi)) -- all in
+// [2^23, 2^24), where the float's ulp is 1, so the rounding is the floor.  The
+// low bits of the result's bit pattern are then (8 j + f) mod 32 with
+// f = floor(r 12/pi) in [-4, 3]: bits 0-3 index the 16 signed rows and bit 4
+// is bit 1 of j' = j - [r < 0], the quadrant of x below it, whose sin and cos
+// are negative for j' mod 4 in {2, 3}.  The floor differs from the segment of
+// the exact r only where r 12/pi lies within an FP32 rounding of an integer,
+// i.e. at a node k pi/12, where both adjacent segments are valid.
+__device__ __forceinline__ uint32_t seg_code(float r, uint32_t jb) {
+  const float c = __fmaf_rn(__uint_as_float(jb), 8.0f, PTRIG_SEG_BASE_C);
+  return __float_as_uint(__fmaf_rd(r, PTRIG_12_OVER_PI_F, c));
+}
+
+// Both lanes of a pair with packed FFMA2 (same roundings lane by lane).
+__device__ __forceinline__ float2 seg_code2(float2 r, float2 y) {
+  const float2 c = __ffma2_rn(y, make_float2(8.0f, 8.0f), make_float2(PTRIG_SEG_BASE_C, PTRIG_SEG_BASE_C));
+  return __ffma2_rd(r, make_float2(PTRIG_12_OVER_PI_F, PTRIG_12_OVER_PI_F), c);
+}
+
+// Quadrant sign of sin and cos at bit 31 (bit 4 of the row code).
+__device__ __forceinline__ uint32_t seg_sign(uint32_t code) { return (code << 27) & 0x80000000u; }
+
+// Paper's segment (0..5, of u) and the row's parts, for the segment dump:
+// rows 0-3 hold r >= 0 and kq = i, rows 4-7 r < 0 and kq = 7 - i, and the
+// rows 8-15 repeat that with the other parity of j'; p = j & 1 = (j' & 1) xor
+// [r < 0], and the segment is kq for even j, 5 - kq for odd j.
+__device__ __forceinline__ uint32_t seg_of_code(uint32_t code) {
+  const uint32_t i = code & 15u, f = i & 7u;
+  const uint32_t neg = f >> 2;
+  const uint32_t kq = neg ? 7u - f : f;
+  const uint32_t p = ((i >> 3) ^ neg) & 1u;
+  return p ? 5u - kq : kq;
+}
+
+// N and D of one lane from its row.
+__device__ __forceinline__ float2 seg_nd(const STab *tab, uint32_t code, float r) {
+  const uint32_t i = code & 15u;
+  const float2 a = tab->a[i];
+  const float2 b = tab->b[i];
+  return make_float2(__fmaf_rn(a.x, r, b.x), __fmaf_rn(a.y, r, b.y));
+}
+
+// Pair form: two angles through the packed reduction, row code and radicand.
+// m0 (and m1 for sincos) are the lanes' values without the quadrant sign of
+// sin and cos; code0 / code1 carry it in bit 4 (tan needs none: the rows fold
+// its sign into D).
 template <int OP>
-__device__ __forceinline__ void proposed_pair_mag(float2 x, const float4 *tab, float2 &m0, float2 &m1,
-                                                  uint32_t &s0, uint32_t &s1) {
-  const RedF2 red = reduce_fast2(x);
-  const float2 t = make_float2(fabsf(red.r.x), fabsf(red.r.y));
-  // segment_kq() for both lanes with packed FFMA2 / FADD2
-  const float2 z = __ffma2_rn(t, make_float2(PTRIG_12_OVER_PI_F, PTRIG_12_OVER_PI_F), make_float2(-0.5f, -0.5f));
-  const float2 v = __fadd2_rn(z, make_float2(PTRIG_RINT_MAGIC_F, PTRIG_RINT_MAGIC_F));
-  const uint32_t i0 = ((red.jb0 & 1u) << 2) | (__float_as_uint(v.x) & 3u);
-  const uint32_t i1 = ((red.jb1 & 1u) << 2) | (__float_as_uint(v.y) & 3u);
-  const float4 c0 = tab[i0];
-  const float4 c1 = tab[i1];
-  const float2 N = make_float2(__fmaf_rn(c0.x, t.x, c0.y), __fmaf_rn(c1.x, t.y, c1.y));
-  const float2 D = make_float2(__fmaf_rn(c0.z, t.x, c0.w), __fmaf_rn(c1.z, t.y, c1.w));
-  const uint32_t J = __byte_perm(red.jb0, red.jb1, 0x4000);
-  const uint32_t R = __byte_perm(__float_as_uint(red.r.x), __float_as_uint(red.r.y), 0x7030);
-  const uint32_t A = J << 6;  // j1 at bits 15 / 31
-  const uint32_t P = J << 7;  // p at bits 15 / 31
+__device__ __forceinline__ void proposed_pair(float2 x, const STab *tab, float2 &m0, float2 &m1, uint32_t &code0,
+                                              uint32_t &code1) {
+  const float2 y = __ffma2_rn(x, make_float2(PTRIG_2_OVER_PI_F, PTRIG_2_OVER_PI_F),
+                              make_float2(PTRIG_RINT_MAGIC_F, PTRIG_RINT_MAGIC_F));
+  const float2 jf = __fadd2_rn(y, make_float2(-PTRIG_RINT_MAGIC_F, -PTRIG_RINT_MAGIC_F));
+  float2 r = __ffma2_rn(jf, make_float2(-PTRIG_PIO2_F1, -PTRIG_PIO2_F1), x);
+  r = __ffma2_rn(jf, make_float2(-PTRIG_PIO2_F2, -PTRIG_PIO2_F2), r);
+  r = __ffma2_rn(jf, make_float2(-PTRIG_PIO2_F3, -PTRIG_PIO2_F3), r);
+  const float2 v = seg_code2(r, y);
+  code0 = __float_as_uint(v.x);
+  code1 = __float_as_uint(v.y);
+  const float2 nd0 = seg_nd(tab, code0, r.x);
+  const float2 nd1 = seg_nd(tab, code1, r.y);
+  const float2 N = make_float2(nd0.x, nd1.x);
+  const float2 D = make_float2(nd0.y, nd1.y);
   if (OP == OP_TAN) {
     m0 = __fmul2_rn(N, make_float2(rcp_approx(D.x), rcp_approx(D.y)));
-    s0 = P ^ R;
   } else {
     const float2 h2 = __ffma2_rn(N, N, __fmul2_rn(D, D));
     const float2 rs = make_float2(rsqrt_approx(h2.x), rsqrt_approx(h2.y));
-    if (OP == OP_SIN || OP == OP_SINCOS) {
-      m0 = __fmul2_rn(N, rs);
-      s0 = A ^ (R & ~P);
-    }
-    if (OP == OP_COS) {
-      m0 = __fmul2_rn(D, rs);
-      s0 = A ^ (P & ~R);
-    }
-    if (OP == OP_SINCOS) {
-      m1 = __fmul2_rn(D, rs);
-      s1 = A ^ (P & ~R);
-    }
+    if (OP == OP_SIN || OP == OP_SINCOS) m0 = __fmul2_rn(N, rs);
+    if (OP == OP_COS) m0 = __fmul2_rn(D, rs);
+    if (OP == OP_SINCOS) m1 = __fmul2_rn(D, rs);
   }
 }
 
-// FULL = false: the caller guarantees |x| <= 2^20 (FP32 reduction only).
+// FP32 reduction with the side path above lim.
 template <bool FULL>
-__device__ __forceinline__ RedF reduce_sel(float x) {
-  return FULL ? reduce_f32(x) : reduce_fast(x);
+__device__ __forceinline__ RedF reduce_sel(float x, float lim = PTRIG_FAST_LIMIT_F) {
+  if (!FULL) return reduce_fast(x);
+  RedF red = reduce_fast(x);
+  if (__builtin_expect(!(fabsf(x) <= lim), 0)) red = reduce_slow_f32(x);
+  return red;
 }
 
 // True if x needs the FP64 / Payne-Hanek side path (or is NaN / infinite).
@@ -328,33 +381,28 @@ struct Proposed {
   static constexpr int NOUT = (OP == OP_SINCOS) ? 2 : 1;
   static constexpr bool HAS_SLOW = true;
   static constexpr bool HAS_PAIR = true;
-  static constexpr bool USES_TABLE = true;  // coefficient table in shared memory
-  static constexpr int GROUP = 1;           // 16-byte accesses (32-byte ones measured slower)
-  // FP32 storage evaluated in float2 pairs as well: fewer instructions for all
-  // four functions, faster for sin and cos (+1-3%), slower for tan and sincos.
-  static constexpr bool PAIR_F32 = (OP == OP_SIN || OP == OP_COS);
-  __device__ __forceinline__ static void eval_pair_mag(float2 x, const float4 *tab, float2 &m0, float2 &m1,
-                                                       uint32_t &s0, uint32_t &s1) {
-    proposed_pair_mag<OP>(x, tab, m0, m1, s0, s1);
+  static constexpr bool USES_TABLE = true;  // signed rows in shared memory
+  static constexpr bool SIGNED_OUT = (OP != OP_TAN);  // quadrant sign applied by the caller
+  static constexpr int GROUP = 1;           // 16-byte accesses
+  // The FP32 reduction bound of the signed-row index.
+  __device__ __forceinline__ static float limit() { return PTRIG_SEG_LIMIT_F; }
+  __device__ __forceinline__ static void eval_pair(float2 x, const STab *tab, float2 &m0, float2 &m1,
+                                                   uint32_t &c0, uint32_t &c1) {
+    proposed_pair<OP>(x, tab, m0, m1, c0, c1);
   }
   template <bool FULL = true>
-  __device__ __forceinline__ static void eval(float x, const float4 *tab, float &o0, float &o1) {
-    const RedF red = reduce_sel<FULL>(x);
-    const float t = fabsf(red.r);
-    const float4 c = tab[table_index(t, red.jb)];
-    const float N = __fmaf_rn(c.x, t, c.y);
-    const float D = __fmaf_rn(c.z, t, c.w);
-    const Signs g = sign_bits(red.jb, __float_as_uint(red.r));
+  __device__ __forceinline__ static void eval(float x, const STab *tab, float &o0, float &o1) {
+    const RedF red = reduce_sel<FULL>(x, PTRIG_SEG_LIMIT_F);
+    const uint32_t code = seg_code(red.r, red.jb);
+    const float2 nd = seg_nd(tab, code, red.r);
     if (OP == OP_TAN) {
-      o0 = xor_sign(__fmul_rn(N, rcp_approx(D)), g.t);
+      o0 = __fmul_rn(nd.x, rcp_approx(nd.y));
     } else {
-      const float rs = rsqrt_approx(__fmaf_rn(N, N, __fmul_rn(D, D)));
-      if (OP == OP_SIN) o0 = xor_sign(__fmul_rn(N, rs), g.s);
-      if (OP == OP_COS) o0 = xor_sign(__fmul_rn(D, rs), g.c);
-      if (OP == OP_SINCOS) {
-        o0 = xor_sign(__fmul_rn(N, rs), g.s);
-        o1 = xor_sign(__fmul_rn(D, rs), g.c);
-      }
+      const uint32_t sg = seg_sign(code);
+      const float rs = rsqrt_approx(__fmaf_rn(nd.x, nd.x, __fmul_rn(nd.y, nd.y)));
+      if (OP == OP_SIN || OP == OP_SINCOS) o0 = xor_sign(__fmul_rn(nd.x, rs), sg);
+      if (OP == OP_COS) o0 = xor_sign(__fmul_rn(nd.y, rs), sg);
+      if (OP == OP_SINCOS) o1 = xor_sign(__fmul_rn(nd.y, rs), sg);
     }
   }
 };
@@ -377,11 +425,13 @@ struct Taylor {
   static constexpr bool HAS_SLOW = true;
   static constexpr bool HAS_PAIR = false;
   static constexpr bool USES_TABLE = false;
+  static constexpr bool SIGNED_OUT = false;
   static constexpr int GROUP = 2;  // 32-byte accesses
-  __device__ __forceinline__ static void eval_pair_mag(float2, const float4 *, float2 &, float2 &, uint32_t &,
-                                                       uint32_t &) {}
+  __device__ __forceinline__ static float limit() { return PTRIG_FAST_LIMIT_F; }
+  __device__ __forceinline__ static void eval_pair(float2, const STab *, float2 &, float2 &, uint32_t &,
+                                                   uint32_t &) {}
   template <bool FULL = true>
-  __device__ __forceinline__ static void eval(float x, const float4 *, float &o0, float &) {
+  __device__ __forceinline__ static void eval(float x, const STab *, float &o0, float &) {
     const RedF red = reduce_sel<FULL>(x);
     const float t = fabsf(red.r);
     const float u = (red.jb & 1u) ? __fsub_rn(PTRIG_PIO2_F, t) : t;
@@ -485,6 +535,7 @@ struct Storage;
 template <>
 struct Storage<float> {
   static constexpr int EPV = 4;  // elements per 16-byte vector
+  static constexpr bool RANGE_CHECK = true;
   __device__ __forceinline__ static void unpack(const uint4 &v, float (&f)[4]) {
     f[0] = __uint_as_float(v.x);
     f[1] = __uint_as_float(v.y);
@@ -502,6 +553,7 @@ struct Storage<float> {
 template <>
 struct Storage<__half> {
   static constexpr int EPV = 8;
+  static constexpr bool RANGE_CHECK = false;  // |x| <= 65504 < 2^19, or inf / NaN
   __device__ __forceinline__ static float2 to_float2(uint32_t w) {
     __half2 h;
     *reinterpret_cast<uint32_t *>(&h) = w;
@@ -538,6 +590,7 @@ struct Storage<__half> {
 template <>
 struct Storage<__nv_bfloat16> {
   static constexpr int EPV = 8;
+  static constexpr bool RANGE_CHECK = true;
   __device__ __forceinline__ static float2 to_float2(uint32_t w) {
     __nv_bfloat162 h;
     *reinterpret_cast<uint32_t *>(&h) = w;

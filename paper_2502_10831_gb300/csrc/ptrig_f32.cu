@@ -55,11 +55,13 @@ struct CudaMath {
   static constexpr bool HAS_SLOW = false;
   static constexpr bool HAS_PAIR = false;
   static constexpr bool USES_TABLE = false;
+  static constexpr bool SIGNED_OUT = false;
   static constexpr int GROUP = 2;
-  __device__ __forceinline__ static void eval_pair_mag(float2, const float4 *, float2 &, float2 &, uint32_t &,
-                                                       uint32_t &) {}
+  __device__ __forceinline__ static float limit() { return PTRIG_FAST_LIMIT_F; }
+  __device__ __forceinline__ static void eval_pair(float2, const STab *, float2 &, float2 &, uint32_t &,
+                                                   uint32_t &) {}
   template <bool FULL = true>
-  __device__ __forceinline__ static void eval(float x, const float4 *, float &o0, float &o1) {
+  __device__ __forceinline__ static void eval(float x, const STab *, float &o0, float &o1) {
     if (FAST) {
       if (OP == OP_SIN) o0 = __sinf(x);
       if (OP == OP_COS) o0 = __cosf(x);
@@ -97,9 +99,10 @@ ptrig_status launch_cudamath_f32(int op, int fast, const float *x, float *y0, fl
 
 // ------------------------------------------------------------- segment dump
 
-// out = seg | (q << 4): seg = kq (even j) or 5 - kq (odd j); q = quadrant of
-// |x|, i.e. floor(|x| / (pi/2)) mod 4 = j - [r < 0] for x >= 0 and
-// -j - [r > 0] for x < 0 (mod 4).
+// out = seg | (q << 4): seg = the paper's segment of u chosen by the forward
+// kernels' row code (kq for even j, 5 - kq for odd j); q = quadrant of |x|,
+// i.e. floor(|x| / (pi/2)) mod 4 = j - [r < 0] for x >= 0 and -j - [r > 0]
+// for x < 0 (mod 4).
 __global__ void __launch_bounds__(256) k_segment(const float *__restrict__ x, uint8_t *__restrict__ out, size_t n) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)blockDim.x * gridDim.x) {
     const float xv = x[i];
@@ -107,10 +110,8 @@ __global__ void __launch_bounds__(256) k_segment(const float *__restrict__ x, ui
       out[i] = 0xFF;
       continue;
     }
-    const RedF red = reduce_f32(xv);
-    const float t = fabsf(red.r);
-    const uint32_t kq = segment_kq(t);
-    const uint32_t seg = (red.jb & 1u) ? 5u - kq : kq;
+    const RedF red = reduce_f32(xv, PTRIG_SEG_LIMIT_F);
+    const uint32_t seg = seg_of_code(seg_code(red.r, red.jb));
     const uint32_t q = signbit(xv) ? ((0u - red.jb) - (red.r > 0.0f ? 1u : 0u)) & 3u
                                    : (red.jb - (red.r < 0.0f ? 1u : 0u)) & 3u;
     out[i] = (uint8_t)(seg | (q << 4));

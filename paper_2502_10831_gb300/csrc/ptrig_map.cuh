@@ -2,11 +2,10 @@
 //
 // Reads use ld.global.nc.L1::no_allocate and writes st.global.cs: every byte is
 // touched once, so nothing is kept in L1 and the stores are marked
-// evict-first in L2.  Kernels that use the eight-entry coefficient table stage
-// it in shared memory (its 128 bytes span the 32 banks once; a warp's LDS.128
-// lookups of up to eight rows take a few wavefronts at most) and move 16-byte
-// vectors; the table-free kernels (Taylor, CUDA's math functions) move 32-byte
-// groups when the pointers allow it.
+// evict-first in L2.  Kernels of the paper's formulas stage the 16 signed rows
+// in shared memory (two 128-byte halves read with 8-byte loads, which never
+// conflict) and move 16-byte vectors; the table-free kernels (Taylor, CUDA's
+// math functions) move 32-byte groups when the pointers allow it.
 #pragma once
 
 #include <climits>
@@ -16,34 +15,52 @@
 
 namespace ptrig {
 
+// True when every angle of the group lies within the functor's FP32
+// reduction range: the largest |x| against the bound.  A NaN among finite
+// angles drops out of the maximum (fmaxf) and then flows through the fast
+// path, whose every step maps NaN to NaN and whose row index stays in range
+// for any bit pattern.
+template <class F, int E>
+__device__ __forceinline__ bool group_fast(const float (&f)[E]) {
+  float m = fabsf(f[0]);
+#pragma unroll
+  for (int e = 1; e < E; ++e) m = fmaxf(m, fabsf(f[e]));
+  return m <= F::limit();
+}
+
 // Evaluates and stores one 16-byte vector with the FP32 reduction.  Returns
 // false, storing nothing, when an element lies outside the FP32 reduction
-// range (or is NaN / inf); the caller then hands the rest of its work to the
-// full-reduction path.
+// range (or every element is NaN, or one is infinite); the caller then hands
+// the rest of its work to the full-reduction path.  The pair forms evaluate
+// first and check the largest |x| of the vector before the store, so that
+// each pair is unpacked only when it is computed.
 // 16-bit storage with the pair form: lanes stay in float2 from the packed
-// input word to the packed output word; signs are applied to the rounded
-// word with one XOR per output word.
+// input word to the packed output word; the quadrant signs of sin and cos
+// (bit 4 of each lane's row code) are gathered into bits 15 and 31 with one
+// byte permute and applied to the rounded word with one XOR (round-to-nearest
+// is sign-symmetric, so this equals rounding the signed value).  fp16 needs no
+// range check: every finite fp16 lies within the FP32 reduction range, and
+// infinities become NaN in the first reduction step.
 template <typename T, class F>
-__device__ __forceinline__ bool map_vector_fast_h(uint4 v, size_t i, T *y0, T *y1, const float4 *tab) {
+__device__ __forceinline__ bool map_vector_fast_h(uint4 v, size_t i, T *y0, T *y1, const STab *tab) {
   using S = Storage<T>;
   const uint32_t w[4] = {v.x, v.y, v.z, v.w};
-  float2 f[4];
-  bool slow = false;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    f[k] = S::to_float2(w[k]);
-    slow |= needs_slow(f[k].x);
-    slow |= needs_slow(f[k].y);
-  }
-  if (slow) return false;
   uint32_t a[4], b[4];
+  float m = 0.0f;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
+    const float2 f = S::to_float2(w[k]);
+    if constexpr (S::RANGE_CHECK) m = fmaxf(m, fmaxf(fabsf(f.x), fabsf(f.y)));
     float2 m0, m1;
-    uint32_t s0, s1;
-    F::eval_pair_mag(f[k], tab, m0, m1, s0, s1);
-    a[k] = S::from_float2(m0) ^ (s0 & 0x80008000u);
-    if constexpr (F::NOUT == 2) b[k] = S::from_float2(m1) ^ (s1 & 0x80008000u);
+    uint32_t c0, c1;
+    F::eval_pair(f, tab, m0, m1, c0, c1);
+    uint32_t sg = 0;
+    if constexpr (F::SIGNED_OUT) sg = (__byte_perm(c0, c1, 0x4000) << 3) & 0x80008000u;
+    a[k] = S::from_float2(m0) ^ sg;
+    if constexpr (F::NOUT == 2) b[k] = S::from_float2(m1) ^ sg;
+  }
+  if constexpr (S::RANGE_CHECK) {
+    if (!(m <= F::limit())) return false;
   }
   st_stream(reinterpret_cast<uint4 *>(y0) + i, make_uint4(a[0], a[1], a[2], a[3]));
   if constexpr (F::NOUT == 2) st_stream(reinterpret_cast<uint4 *>(y1) + i, make_uint4(b[0], b[1], b[2], b[3]));
@@ -51,49 +68,48 @@ __device__ __forceinline__ bool map_vector_fast_h(uint4 v, size_t i, T *y0, T *y
 }
 
 // FP32 storage with the pair form: the four angles of a vector as two float2
-// pairs through the packed reduction and evaluation; the pair sign words hold
-// lane 0's sign at bit 15 and lane 1's at bit 31.
+// pairs through the packed reduction and evaluation; each lane takes its
+// quadrant sign from its own row code.
 template <class F>
 __device__ __forceinline__ bool map_vector_fast_f32pair(uint4 v, size_t i, float *y0, float *y1,
-                                                        const float4 *tab) {
+                                                        const STab *tab) {
   const float f[4] = {__uint_as_float(v.x), __uint_as_float(v.y), __uint_as_float(v.z), __uint_as_float(v.w)};
-  bool slow = false;
-#pragma unroll
-  for (int e = 0; e < 4; ++e) slow |= needs_slow(f[e]);
-  if (slow) return false;
   uint32_t a[4], b[4];
+  float m = 0.0f;
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
+    m = fmaxf(m, fmaxf(fabsf(f[2 * k]), fabsf(f[2 * k + 1])));
     float2 m0, m1;
-    uint32_t s0, s1;
-    F::eval_pair_mag(make_float2(f[2 * k], f[2 * k + 1]), tab, m0, m1, s0, s1);
-    a[2 * k] = __float_as_uint(m0.x) ^ ((s0 << 16) & 0x80000000u);
-    a[2 * k + 1] = __float_as_uint(m0.y) ^ (s0 & 0x80000000u);
+    uint32_t c0, c1;
+    F::eval_pair(make_float2(f[2 * k], f[2 * k + 1]), tab, m0, m1, c0, c1);
+    uint32_t s0 = 0, s1 = 0;
+    if constexpr (F::SIGNED_OUT) {
+      s0 = seg_sign(c0);
+      s1 = seg_sign(c1);
+    }
+    a[2 * k] = __float_as_uint(m0.x) ^ s0;
+    a[2 * k + 1] = __float_as_uint(m0.y) ^ s1;
     if constexpr (F::NOUT == 2) {
-      b[2 * k] = __float_as_uint(m1.x) ^ ((s1 << 16) & 0x80000000u);
-      b[2 * k + 1] = __float_as_uint(m1.y) ^ (s1 & 0x80000000u);
+      b[2 * k] = __float_as_uint(m1.x) ^ s0;
+      b[2 * k + 1] = __float_as_uint(m1.y) ^ s1;
     }
   }
+  if (!(m <= F::limit())) return false;
   st_stream(reinterpret_cast<uint4 *>(y0) + i, make_uint4(a[0], a[1], a[2], a[3]));
   if constexpr (F::NOUT == 2) st_stream(reinterpret_cast<uint4 *>(y1) + i, make_uint4(b[0], b[1], b[2], b[3]));
   return true;
 }
 
 template <typename T, class F>
-__device__ __forceinline__ bool map_vector_fast(uint4 v, size_t i, T *y0, T *y1, const float4 *tab) {
+__device__ __forceinline__ bool map_vector_fast(uint4 v, size_t i, T *y0, T *y1, const STab *tab) {
   if constexpr (F::HAS_PAIR && sizeof(T) == 2) return map_vector_fast_h<T, F>(v, i, y0, y1, tab);
-  if constexpr (F::HAS_PAIR && sizeof(T) == 4) {
-    if constexpr (F::PAIR_F32) return map_vector_fast_f32pair<F>(v, i, y0, y1, tab);
-  }
+  if constexpr (F::HAS_PAIR && sizeof(T) == 4) return map_vector_fast_f32pair<F>(v, i, y0, y1, tab);
   using S = Storage<T>;
   constexpr int E = S::EPV;
   float f[E], o0[E], o1[E];
   S::unpack(v, f);
   if constexpr (F::HAS_SLOW) {
-    bool slow = false;
-#pragma unroll
-    for (int e = 0; e < E; ++e) slow |= needs_slow(f[e]);
-    if (slow) return false;
+    if (!group_fast<F, E>(f)) return false;
   }
 #pragma unroll
   for (int e = 0; e < E; ++e) F::template eval<false>(f[e], tab, o0[e], o1[e]);
@@ -104,12 +120,12 @@ __device__ __forceinline__ bool map_vector_fast(uint4 v, size_t i, T *y0, T *y1,
 
 // Vectors i, i + stride, ... < nvec with the full reduction (FP32 Cody-Waite,
 // FP64 Cody-Waite or Payne-Hanek per element).  Out of line and reached only
-// after a thread met an angle beyond 2^20, so the pipelined loop carries no
-// call and no FP64 / Payne-Hanek register state.
+// after a thread met an angle beyond the FP32 reduction range, so the
+// pipelined loop carries no call and no FP64 / Payne-Hanek register state.
 template <typename T, class F>
 static __device__ __noinline__ void map_resume_full(const T *__restrict__ x, T *__restrict__ y0,
                                                     T *__restrict__ y1, size_t i, size_t nvec, size_t stride,
-                                                    const float4 *tab) {
+                                                    const STab *tab) {
   using S = Storage<T>;
   constexpr int E = S::EPV;
   for (; i < nvec; i += stride) {
@@ -133,10 +149,7 @@ __device__ __forceinline__ bool wide_vector_eval(uint4 v, uint4 &o0, uint4 &o1) 
   float f[E];
   S::unpack(v, f);
   if constexpr (F::HAS_SLOW) {
-    bool slow = false;
-#pragma unroll
-    for (int e = 0; e < E; ++e) slow |= needs_slow(f[e]);
-    if (slow) return false;
+    if (!group_fast<F, E>(f)) return false;
   }
   float r0[E], r1[E];
 #pragma unroll
@@ -192,8 +205,8 @@ __device__ __forceinline__ void st_group32(void *base, size_t u, const Vec32 &v)
 template <typename T, class F, int D, bool PERSIST>
 __device__ __forceinline__ void map_stream(const T *__restrict__ x, T *__restrict__ y0, T *__restrict__ y1,
                                            size_t n) {
-  __shared__ float4 s_tab[8];
-  if (threadIdx.x < 8) s_tab[threadIdx.x] = c_tab_f32[threadIdx.x];
+  __shared__ STab s_tab;
+  stage_stab(&s_tab);
   __syncthreads();
   using S = Storage<T>;
   constexpr int E = S::EPV;
@@ -201,7 +214,7 @@ __device__ __forceinline__ void map_stream(const T *__restrict__ x, T *__restric
   if (blockIdx.x == 0) {  // the n % E elements after the last whole vector
     for (size_t k = nvec * E + threadIdx.x; k < n; k += blockDim.x) {
       float o0, o1;
-      F::template eval<true>(S::load1(x + k), s_tab, o0, o1);
+      F::template eval<true>(S::load1(x + k), &s_tab, o0, o1);
       S::store1(y0 + k, o0);
       if constexpr (F::NOUT == 2) S::store1(y1 + k, o1);
     }
@@ -236,7 +249,7 @@ __device__ __forceinline__ void map_stream(const T *__restrict__ x, T *__restric
           const size_t jn = ii + (size_t)D * step;
           if (jn < end) buf[d] = ld_stream(xv + jn);
         }
-        if (!map_vector_fast<T, F>(cur, ii, y0, y1, s_tab)) {
+        if (!map_vector_fast<T, F>(cur, ii, y0, y1, &s_tab)) {
           resume = ii + 1;  // +1 so that 0 means "finished"
           goto full;
         }
@@ -245,7 +258,7 @@ __device__ __forceinline__ void map_stream(const T *__restrict__ x, T *__restric
   }
   return;
 full:
-  map_resume_full<T, F>(x, y0, y1, resume - 1, end, step, s_tab);
+  map_resume_full<T, F>(x, y0, y1, resume - 1, end, step, &s_tab);
 }
 
 // The same stream over 32-byte groups (two 16-byte vectors per access), for
@@ -352,13 +365,13 @@ void launch_k_map(unsigned grid, int block, cudaStream_t s, const T *x, T *y0, T
 template <typename T, class F>
 __global__ void __launch_bounds__(512) k_map_scalar(const T *__restrict__ x, T *__restrict__ y0,
                                                     T *__restrict__ y1, size_t n) {
-  __shared__ float4 s_tab[8];
-  if (threadIdx.x < 8) s_tab[threadIdx.x] = c_tab_f32[threadIdx.x];
+  __shared__ STab s_tab;
+  stage_stab(&s_tab);
   __syncthreads();
   using S = Storage<T>;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)blockDim.x * gridDim.x) {
     float o0, o1;
-    F::template eval<true>(S::load1(x + i), s_tab, o0, o1);
+    F::template eval<true>(S::load1(x + i), &s_tab, o0, o1);
     S::store1(y0 + i, o0);
     if constexpr (F::NOUT == 2) S::store1(y1 + i, o1);
   }

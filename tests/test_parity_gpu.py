@@ -99,19 +99,29 @@ def test_edge_values(B, oracle):
             assert np.all(yz == 0.0) and list(np.signbit(yz)) == [False, True]
 
 
-@pytest.mark.parametrize("func", ("sin", "tan"))
+@pytest.mark.parametrize("func", ("sin", "cos", "tan", "sincos"))
 def test_large_arguments(B, oracle, func):
-    """|x| log-uniform in [1, 1e5] (FP32 reduction), in (2^20, 2^31) (FP64
-    Cody-Waite side path) and up to the largest float (Payne-Hanek)."""
+    """|x| log-uniform in [1, 1e5] (FP32 reduction), in (2^19, 2^31) (FP64
+    Cody-Waite side path) and up to the largest float (Payne-Hanek), for every
+    function (sincos: both outputs)."""
     big = workloads.large(1 << 20)
     r = np.random.default_rng(4)
-    mid = (2.0 ** r.uniform(20.0, 31.0, 1 << 16) * r.choice([-1, 1], 1 << 16)).astype(np.float32)
+    mid = (2.0 ** r.uniform(19.0, 31.0, 1 << 16) * r.choice([-1, 1], 1 << 16)).astype(np.float32)
     huge = (10.0 ** r.uniform(9.5, 38.5, 4096) * r.choice([-1, 1], 4096)).astype(np.float32)
     x = np.concatenate([big, mid, huge[np.isfinite(huge)]])
     xd = x.astype(np.float64)
-    y = _run(B, func, x)
-    ref, _ = P.reference_with_gpu_segments(oracle, func, xd, _segments(B, x))
-    P.check_values(oracle, func, xd, y, ref)
+    seg = _segments(B, x)
+    if func == "sincos":
+        xt = _dev(x)
+        s, c = torch.empty_like(xt), torch.empty_like(xt)
+        B.ptrig_sincos_f32(xt, s, c)
+        torch.cuda.synchronize()
+        outs = {"sin": s.cpu().numpy(), "cos": c.cpu().numpy()}
+    else:
+        outs = {func: _run(B, func, x)}
+    for f, y in outs.items():
+        ref, _ = P.reference_with_gpu_segments(oracle, f, xd, seg)
+        P.check_values(oracle, f, xd, y, ref)
 
 
 @pytest.fixture(scope="module")

@@ -93,3 +93,75 @@ def test_precision_report(B, oracle):
         os.makedirs(out, exist_ok=True)
         with open(os.path.join(out, "precision_report.json"), "w") as fh:
             json.dump(report, fh, indent=1)
+
+
+def _threaded(fn, x, parts=16):
+    """fn over slices of x on host threads (the oracle's C calls release the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+    chunks = np.array_split(x, parts)
+    with ThreadPoolExecutor(max_workers=parts) as ex:
+        return np.concatenate(list(ex.map(fn, chunks)))
+
+
+def test_precision_report_large_arguments(B, oracle):
+    """The precision configuration's large-argument set: 2^24 FP32 angles with
+    |x| log-uniform in [1, 1e5] (FP32 reduction), and 2^20 samples of each
+    reduction side path -- |x| log-uniform in [2^19, 2^31) (FP64 Cody-Waite)
+    and in [2^31, 2^127) (Payne-Hanek).  Per function (sincos: both outputs
+    of the fused kernel) the error against the FP64 oracle and the oracle's
+    against numpy's float64 functions (the method's own error)."""
+    r = np.random.default_rng(11)
+    sets = {"log_uniform_1_1e5_2p24": workloads.large(1 << 24)}
+    for name, lo, hi in (("side_fp64_cody_waite_2p19_2p31", 19.0, 31.0), ("side_payne_hanek_2p31_2p127", 31.0, 127.0)):
+        sets[name] = (2.0 ** r.uniform(lo, hi, 1 << 20) * r.choice([-1.0, 1.0], 1 << 20)).astype(np.float32)
+    report = {}
+    for sname, x in sets.items():
+        xd = x.astype(np.float64)
+        xt = torch.from_numpy(x).cuda()
+        seg = torch.empty(xt.shape, dtype=torch.uint8, device="cuda")
+        B.ptrig_segment_f32(xt, seg)
+        ys = {}
+        for f in ("sin", "cos", "tan"):
+            y = torch.empty_like(xt)
+            getattr(B, f"ptrig_{f}_f32")(xt, y)
+            ys[f] = y
+        s, c = torch.empty_like(xt), torch.empty_like(xt)
+        B.ptrig_sincos_f32(xt, s, c)
+        torch.cuda.synchronize()
+        segh = seg.cpu().numpy()
+        cosr = np.abs(_threaded(lambda a: oracle.proposed("cos", a), xd))
+        # the oracle with the segment the GPU chose (near a node either is valid)
+        idx = np.arange(xd.size)
+        refs = {f: _threaded(lambda i: P.reference_with_gpu_segments(oracle, f, xd[i], segh[i])[0], idx)
+                for f in ("sin", "cos", "tan")}
+        outs = [(f, f, ys[f]) for f in ("sin", "cos", "tan")] + [("sincos.sin", "sin", s), ("sincos.cos", "cos", c)]
+        sec = {}
+        for label, f, t in outs:
+            got = t.cpu().numpy().astype(np.float64)
+            ref = refs[f]
+            exact = getattr(np, f)(xd)
+            if f == "tan":
+                keep = cosr >= 1e-3
+                e_gpu = np.abs(got[keep] - ref[keep]) / np.abs(ref[keep])
+                e_method = np.abs(ref[keep] - exact[keep]) / np.abs(exact[keep])
+                kind = "relative, |cos| >= 1e-3"
+                tol = 1e-5
+            else:
+                e_gpu = np.abs(got - ref)
+                e_method = np.abs(ref - exact)
+                kind = "absolute"
+                tol = 1e-6
+            sec[label] = {"vs_oracle": {"max": float(e_gpu.max()), "mean": float(e_gpu.mean()), "kind": kind,
+                                        "tolerance": tol},
+                          "method_vs_numpy_fp64": {"max": float(e_method.max()), "mean": float(e_method.mean()),
+                                                   "kind": kind},
+                          "n": int(e_gpu.size)}
+            assert e_gpu.max() <= tol, (sname, label, e_gpu.max())
+        report[sname] = sec
+        del xt, seg, ys, s, c
+        torch.cuda.empty_cache()
+    out = os.environ.get("PTRIG_REPORT_DIR")
+    if out:
+        os.makedirs(out, exist_ok=True)
+        with open(os.path.join(out, "precision_report_large.json"), "w") as fh:
+            json.dump(report, fh, indent=1)
