@@ -124,6 +124,13 @@ def exported_symbols() -> list[str]:
 
 # --------------------------------------------------------------- marshalling
 
+# bytes per element of each entry point's arrays, by name suffix
+_ESIZE = {"f32": 4, "f16": 2, "bf16": 2, "f64": 8}
+
+
+def _esize(name: str) -> int:
+    return _ESIZE[name.rsplit("_", 1)[1]]
+
 
 def _ptr(a) -> int | None:
     if a is None:
@@ -135,6 +142,51 @@ def _ptr(a) -> int | None:
 
 def _count(a) -> int:
     return a.numel()
+
+
+def _buffers(name: str, n: int, *bufs):
+    """Checks the tensors among `bufs` -- (tensor or int or None, bytes per
+    element) pairs -- before any launch: each must be a contiguous CUDA tensor
+    (or pinned host tensor, which the device reaches directly) holding at
+    least n elements of that width, the CUDA ones all on one device.  Raw
+    integer addresses are the caller's responsibility.  Returns that device
+    (None if no CUDA tensor was passed)."""
+    dev = None
+    for b, esize in bufs:
+        if b is None or isinstance(b, int):
+            continue
+        if not b.is_cuda and not b.is_pinned():
+            raise ValueError(f"{name}: arrays must be CUDA tensors or pinned host tensors")
+        if not b.is_contiguous():
+            raise ValueError(f"{name}: arrays must be contiguous")
+        if b.element_size() != esize:
+            raise ValueError(f"{name}: arrays hold {esize}-byte elements, got {b.dtype}")
+        if b.numel() < n:
+            raise ValueError(f"{name}: an array holds {b.numel()} elements, fewer than n = {n}")
+        if not b.is_cuda:
+            continue
+        if dev is None:
+            dev = b.device
+        elif b.device != dev:
+            raise ValueError(f"{name}: arrays on different devices ({dev}, {b.device})")
+    return dev
+
+
+class _on:
+    """Makes `dev` torch's current device for the launch (no-op for None)."""
+
+    def __init__(self, dev):
+        self.dev = dev
+
+    def __enter__(self):
+        if self.dev is not None:
+            import torch
+            self.ctx = torch.cuda.device(self.dev)
+            self.ctx.__enter__()
+
+    def __exit__(self, *exc):
+        if self.dev is not None:
+            self.ctx.__exit__(*exc)
 
 
 def _stream(stream) -> int | None:
@@ -151,19 +203,26 @@ def _check(status: int, where: str):
         raise PtrigError(status, where)
 
 
-def _unary(name):
+def _unary(name, out_esize=None):
+    es = _esize(name)
+    oes = es if out_esize is None else out_esize
+
     def f(x, y, n=None, stream=None):
         n = _count(x) if n is None else n
-        _check(getattr(_load(), name)(_ptr(x), _ptr(y), n, _stream(stream)), name)
+        with _on(_buffers(name, n, (x, es), (y, oes))):
+            _check(getattr(_load(), name)(_ptr(x), _ptr(y), n, _stream(stream)), name)
     f.__name__ = name
     f.__doc__ = f"{name}(x, y, n=None, stream=None): see include/ptrig.h"
     return f
 
 
 def _binary_out(name):
+    es = _esize(name)
+
     def f(x, y0, y1, n=None, stream=None):
         n = _count(x) if n is None else n
-        _check(getattr(_load(), name)(_ptr(x), _ptr(y0), _ptr(y1), n, _stream(stream)), name)
+        with _on(_buffers(name, n, (x, es), (y0, es), (y1, es))):
+            _check(getattr(_load(), name)(_ptr(x), _ptr(y0), _ptr(y1), n, _stream(stream)), name)
     f.__name__ = name
     f.__doc__ = f"{name}(x, a, b, n=None, stream=None): see include/ptrig.h"
     return f
@@ -171,36 +230,41 @@ def _binary_out(name):
 
 for _name, _args in SIGNATURES.items():
     if _args == [_P, _P, _SZ, _P]:
-        globals()[_name] = _unary(_name)
+        globals()[_name] = _unary(_name, 1 if _name == "ptrig_segment_f32" else None)
     elif _args == [_P, _P, _P, _SZ, _P]:
         globals()[_name] = _binary_out(_name)
 
 
 def ptrig_taylor_n_f32(func, nterms, x, y, n=None, stream=None):
     n = _count(x) if n is None else n
-    _check(_load().ptrig_taylor_n_f32(func, nterms, _ptr(x), _ptr(y), n, _stream(stream)),
-           "ptrig_taylor_n_f32")
+    with _on(_buffers("ptrig_taylor_n_f32", n, (x, 4), (y, 4))):
+        _check(_load().ptrig_taylor_n_f32(func, nterms, _ptr(x), _ptr(y), n, _stream(stream)),
+               "ptrig_taylor_n_f32")
 
 
 def ptrig_faithful_f64(func, x, y, n=None, stream=None):
     """The paper's Algorithms 1-6 (FISR, 0.261 selector, pole guard) in FP64."""
     n = _count(x) if n is None else n
-    _check(_load().ptrig_faithful_f64(func, _ptr(x), _ptr(y), n, _stream(stream)), "ptrig_faithful_f64")
+    with _on(_buffers("ptrig_faithful_f64", n, (x, 8), (y, 8))):
+        _check(_load().ptrig_faithful_f64(func, _ptr(x), _ptr(y), n, _stream(stream)), "ptrig_faithful_f64")
 
 
 def ptrig_cudamath_f32(func, fast, x, y0, y1=None, n=None, stream=None):
     n = _count(x) if n is None else n
-    _check(_load().ptrig_cudamath_f32(func, fast, _ptr(x), _ptr(y0), _ptr(y1), n, _stream(stream)),
-           "ptrig_cudamath_f32")
+    with _on(_buffers("ptrig_cudamath_f32", n, (x, 4), (y0, 4), (y1, 4))):
+        _check(_load().ptrig_cudamath_f32(func, fast, _ptr(x), _ptr(y0), _ptr(y1), n, _stream(stream)),
+               "ptrig_cudamath_f32")
 
 
 def ptrig_sincostan_loss_f32(x, w, v, u, clamp_lo, clamp_hi, loss, gx, n=None, stream=None):
     """Fused loss sum(w sin + v cos + u clamp(tan)) into the device double
     `loss`, and its gradient into gx.  See include/ptrig.h."""
     n = _count(x) if n is None else n
-    _check(_load().ptrig_sincostan_loss_f32(_ptr(x), _ptr(w), _ptr(v), _ptr(u), n, clamp_lo, clamp_hi,
-                                            _ptr(loss), _ptr(gx), _stream(stream)),
-           "ptrig_sincostan_loss_f32")
+    with _on(_buffers("ptrig_sincostan_loss_f32", n, (x, 4), (w, 4), (v, 4), (u, 4), (gx, 4))):
+        _buffers("ptrig_sincostan_loss_f32", 1, (loss, 8))
+        _check(_load().ptrig_sincostan_loss_f32(_ptr(x), _ptr(w), _ptr(v), _ptr(u), n, clamp_lo, clamp_hi,
+                                                _ptr(loss), _ptr(gx), _stream(stream)),
+               "ptrig_sincostan_loss_f32")
 
 
 def ptrig_status_string(status: int) -> str:
@@ -232,9 +296,19 @@ def ptrig_get_launch_config(family):
 
 def ptrig_batch_run_noalloc(device_descs, count, stream=None):
     """Ragged batch without any device allocation: device_descs is the device
-    address (or a tensor) of `count` ptrig_desc structs.  See include/ptrig.h."""
-    _check(_load().ptrig_batch_run_noalloc(_ptr(device_descs), count, _stream(stream)),
-           "ptrig_batch_run_noalloc")
+    address (or a CUDA tensor of at least count * 40 bytes) of `count`
+    ptrig_desc structs.  See include/ptrig.h."""
+    dev = None
+    if device_descs is not None and not isinstance(device_descs, int):
+        need = count * ctypes.sizeof(ptrig_desc)
+        have = device_descs.numel() * device_descs.element_size()
+        if not device_descs.is_cuda or not device_descs.is_contiguous() or have < need:
+            raise ValueError(f"ptrig_batch_run_noalloc: descriptors need a contiguous CUDA tensor of at least "
+                             f"{need} bytes, got {have} bytes")
+        dev = device_descs.device
+    with _on(dev):
+        _check(_load().ptrig_batch_run_noalloc(_ptr(device_descs), count, _stream(stream)),
+               "ptrig_batch_run_noalloc")
 
 
 class BatchPlan:

@@ -24,10 +24,25 @@ def _prep(x: torch.Tensor) -> torch.Tensor:
     return x.contiguous()
 
 
+def _check_out(out: torch.Tensor, x: torch.Tensor, what: str = "out") -> None:
+    """out must match x: a contiguous tensor of the same shape, dtype and
+    device (checked before any launch)."""
+    if not isinstance(out, torch.Tensor):
+        raise TypeError(f"{what} must be a tensor")
+    if out.shape != x.shape or out.dtype != x.dtype or out.device != x.device or not out.is_contiguous():
+        raise ValueError(f"{what} must be a contiguous tensor of x's shape {tuple(x.shape)}, dtype {x.dtype} "
+                         f"and device {x.device}; got {tuple(out.shape)}, {out.dtype}, {out.device}"
+                         f"{'' if out.is_contiguous() else ', non-contiguous'}")
+
+
 def forward(func: str, x: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
     """Paper's sin/cos/tan of x (no autograd)."""
     x = _prep(x)
-    y = torch.empty_like(x) if out is None else out
+    if out is None:
+        y = torch.empty_like(x)
+    else:
+        _check_out(out, x)
+        y = out
     getattr(B, f"ptrig_{func}_{_SUFFIX[x.dtype]}")(x, y)
     return y
 
@@ -59,6 +74,8 @@ def derivative(func: str, x: torch.Tensor, gy: torch.Tensor) -> torch.Tensor:
     gy = gy.contiguous()
     if x.dtype not in (torch.float32, torch.float64) or gy.dtype != x.dtype or gy.shape != x.shape:
         raise TypeError("derivative needs matching float32 or float64 x and gy")
+    if gy.device != x.device:
+        raise ValueError(f"gy is on {gy.device}, x on {x.device}")
     gx = torch.empty_like(x)
     getattr(B, f"ptrig_{func}_bwd_{_SUFFIX[x.dtype]}")(x, gy, gx)
     return gx
@@ -133,6 +150,6 @@ def sincostan_loss(x: torch.Tensor, w: torch.Tensor, v: torch.Tensor, u: torch.T
     """Fused sum(w sin(x) + v cos(x) + u clamp(tan(x), lo, hi)) for float32 CUDA
     tensors of one shape, differentiable in x."""
     for t in (x, w, v, u):
-        if not t.is_cuda or t.dtype != torch.float32 or t.shape != x.shape:
-            raise TypeError("sincostan_loss takes float32 CUDA tensors of one shape")
+        if not t.is_cuda or t.dtype != torch.float32 or t.shape != x.shape or t.device != x.device:
+            raise TypeError("sincostan_loss takes float32 CUDA tensors of one shape on one device")
     return _FusedLoss.apply(x, w, v, u, lo, hi)

@@ -135,3 +135,60 @@ def test_cpu_baseline_does_not_reference_the_oracle():
             src = open(os.path.join(d, f)).read()
             for pat in (r"\bimport\s+oracle", r"\bfrom\s+oracle\b", r"ptrig_oracle", r"ptro_"):
                 assert not re.search(pat, src), (f, pat)
+
+
+def test_binding_refuses_mismatched_buffers_before_any_launch():
+    """Tensors that are too small, of another element width or not contiguous
+    are refused on the host (ValueError) before the library is called; so are
+    CPU tensors that are not pinned."""
+    torch = pytest.importorskip("torch")
+    from paper_2502_10831_gb300 import binding as B
+
+    x = torch.zeros(8, dtype=torch.float32)
+    with pytest.raises(ValueError, match="CUDA tensors or pinned"):
+        B.ptrig_sin_f32(x, torch.zeros(8, dtype=torch.float32))
+
+    class Fake:  # stands in for CUDA tensors, so no device is needed
+        def __init__(self, numel, esize, contiguous=True, device="cuda:0"):
+            self._n, self._e, self._c, self.device = numel, esize, contiguous, device
+            self.is_cuda, self.dtype = True, f"{esize}-byte"
+
+        def numel(self):
+            return self._n
+
+        def element_size(self):
+            return self._e
+
+        def is_contiguous(self):
+            return self._c
+
+        def is_pinned(self):
+            return False
+
+        def data_ptr(self):
+            raise AssertionError("the library was reached")
+
+    cases = [
+        ("ptrig_sin_f32", (Fake(8, 4), Fake(7, 4)), "fewer than"),
+        ("ptrig_cos_f16", (Fake(8, 2), Fake(8, 4)), "2-byte"),
+        ("ptrig_tan_f64", (Fake(8, 8), Fake(8, 8, contiguous=False)), "contiguous"),
+        ("ptrig_sincos_bf16", (Fake(8, 2), Fake(8, 2), Fake(4, 2)), "fewer than"),
+        ("ptrig_sin_bwd_f32", (Fake(8, 4), Fake(8, 4), Fake(8, 4, device="cuda:1")), "different devices"),
+        ("ptrig_segment_f32", (Fake(8, 4), Fake(8, 4)), "1-byte"),
+    ]
+    for name, args, msg in cases:
+        with pytest.raises(ValueError, match=msg):
+            getattr(B, name)(*args)
+    with pytest.raises(ValueError, match="descriptors need"):
+        B.ptrig_batch_run_noalloc(Fake(10, 4), 2)  # 40 bytes for 2 descriptors (80 needed)
+
+
+def test_functional_refuses_mismatched_out():
+    torch = pytest.importorskip("torch")
+    from paper_2502_10831_gb300 import functional as Fn
+
+    x = torch.zeros(4, 4)
+    for out in (torch.zeros(4, 3), torch.zeros(4, 4, dtype=torch.float64), torch.zeros(4, 8)[:, ::2]):
+        with pytest.raises(ValueError):
+            Fn._check_out(out, x)
+    Fn._check_out(torch.zeros(4, 4), x)
