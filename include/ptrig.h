@@ -188,6 +188,15 @@ ptrig_status ptrig_segment_f32(const float *x, uint8_t *out, size_t n, ptrig_str
 ptrig_status ptrig_cudamath_f32(int func, int fast, const float *x, float *y0, float *y1, size_t n,
                                 ptrig_stream stream);
 
+/* FP64 FMA throughput probe, the roofline of the FP64 data path (no
+ * counterpart in the paper: a measurement kernel).  Launches nsink / 256
+ * blocks of 256 threads; each thread runs eight independent chains of iters
+ * FP64 FMAs (16 * iters FLOPs) and writes one double to sink[thread].  The
+ * caller times it (events on `stream`) and divides the FLOPs by the time.
+ * sink: nsink device doubles, nsink a multiple of 256 (PTRIG_ERR_INVALID_ARG
+ * otherwise, or for iters <= 0 or sink == NULL); nsink == 0 is a no-op. */
+ptrig_status ptrig_fp64_fma_probe(double *sink, size_t nsink, int iters, ptrig_stream stream);
+
 /* ------------------------------------------------------------------------ */
 /* Launch configuration of the elementwise kernels                          */
 /* ------------------------------------------------------------------------ */

@@ -60,6 +60,7 @@ SIGNATURES = {
     "ptrig_faithful_f64": [_I, _P, _P, _SZ, _P],
     "ptrig_segment_f32": [_P, _P, _SZ, _P],
     "ptrig_cudamath_f32": [_I, _I, _P, _P, _P, _SZ, _P],
+    "ptrig_fp64_fma_probe": [_P, _SZ, _I, _P],
     "ptrig_set_launch_config": [_I, _I, _I, _I],
     "ptrig_get_launch_config": [_I, _P, _P, _P],
     "ptrig_batch_plan_create": [_P, _P, _SZ, _I],
@@ -265,6 +266,14 @@ def ptrig_sincostan_loss_f32(x, w, v, u, clamp_lo, clamp_hi, loss, gx, n=None, s
         _check(_load().ptrig_sincostan_loss_f32(_ptr(x), _ptr(w), _ptr(v), _ptr(u), n, clamp_lo, clamp_hi,
                                                 _ptr(loss), _ptr(gx), _stream(stream)),
                "ptrig_sincostan_loss_f32")
+
+
+def ptrig_fp64_fma_probe(sink, iters, nsink=None, stream=None):
+    """Measurement kernel: nsink / 256 blocks of 256 threads, each thread
+    16 * iters FP64 FLOPs (8 FMA chains); sink receives one double per thread."""
+    nsink = _count(sink) if nsink is None else nsink
+    with _on(_buffers("ptrig_fp64_fma_probe", nsink, (sink, 8))):
+        _check(_load().ptrig_fp64_fma_probe(_ptr(sink), nsink, iters, _stream(stream)), "ptrig_fp64_fma_probe")
 
 
 def ptrig_status_string(status: int) -> str:

@@ -22,7 +22,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libptrig.so")
 
-SOURCES = ["ptrig_api.cu", "ptrig_f32.cu", "ptrig_half.cu", "ptrig_bwd.cu", "ptrig_batch.cu", "ptrig_faithful.cu"]
+SOURCES = ["ptrig_api.cu", "ptrig_f32.cu", "ptrig_half.cu", "ptrig_bwd.cu", "ptrig_batch.cu", "ptrig_faithful.cu",
+           "ptrig_diag.cu"]
 HEADERS = ["ptrig_device.cuh", "ptrig_map.cuh", "ptrig_internal.h", "ptrig_constants.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

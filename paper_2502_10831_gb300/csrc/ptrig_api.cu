@@ -1,6 +1,7 @@
 // ptrig_api.cu -- extern "C" entry points of libptrig (declared in ptrig.h):
 // argument validation, launch-configuration registry and error reporting.
 #include <atomic>
+#include <climits>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -255,6 +256,12 @@ ptrig_status ptrig_cudamath_f32(int func, int fast, const float *x, float *y0, f
   if (n == 0) return PTRIG_OK;
   if (!x || !y0 || (func == PTRIG_SINCOS && !y1)) return PTRIG_ERR_INVALID_ARG;
   return launch_cudamath_f32(func, fast, x, y0, y1, n, PTRIG_STREAM(stream));
+}
+
+ptrig_status ptrig_fp64_fma_probe(double *sink, size_t nsink, int iters, ptrig_stream stream) {
+  if (nsink == 0) return PTRIG_OK;
+  if (!sink || nsink % 256 != 0 || nsink / 256 > (size_t)INT_MAX || iters <= 0) return PTRIG_ERR_INVALID_ARG;
+  return launch_fp64_fma(sink, nsink, iters, PTRIG_STREAM(stream));
 }
 
 // ------------------------------------------------------- launch configuration

@@ -37,5 +37,6 @@ ptrig_status launch_faithful_f64(int op, const double *x, double *y, size_t n, c
 ptrig_status launch_segment_f32(const float *x, uint8_t *out, size_t n, cudaStream_t s);
 ptrig_status launch_cudamath_f32(int op, int fast, const float *x, float *y0, float *y1, size_t n,
                                  cudaStream_t s);
+ptrig_status launch_fp64_fma(double *sink, size_t nsink, int iters, cudaStream_t s);
 
 }  // namespace ptrig

@@ -70,6 +70,10 @@ def test_host_validation_without_gpu(lib):
     assert lib.ptrig_set_launch_config(0, 256, 3, 0) == 1
     assert lib.ptrig_set_launch_config(9, 256, 4, 0) == 1
     assert lib.ptrig_set_launch_config(0, 256, 16, 0) == 1
+    assert lib.ptrig_fp64_fma_probe(1024, 300, 10, None) == 1  # not a multiple of 256
+    assert lib.ptrig_fp64_fma_probe(1024, 512, 0, None) == 1
+    assert lib.ptrig_fp64_fma_probe(None, 512, 10, None) == 1
+    assert lib.ptrig_fp64_fma_probe(None, 0, 10, None) == 0
 
 
 def test_launch_config_roundtrip(lib):
