@@ -204,15 +204,17 @@ ptrig_status ptrig_fp64_fma_probe(double *sink, size_t nsink, int iters, ptrig_s
 /* Kernel families for ptrig_set_launch_config. */
 typedef enum ptrig_family {
   PTRIG_FAMILY_F32 = 0,         /* proposed FP32 sin, cos, tan */
-  PTRIG_FAMILY_HALF = 1,        /* fp16 storage sin, cos, tan */
+  PTRIG_FAMILY_HALF = 1,        /* fp16 storage sin, cos */
   PTRIG_FAMILY_TAYLOR = 2,      /* Taylor-n FP32 */
   PTRIG_FAMILY_BWD = 3,         /* FP32 derivatives */
-  PTRIG_FAMILY_BF16 = 4,        /* bf16 storage sin, cos, tan */
+  PTRIG_FAMILY_BF16 = 4,        /* bf16 storage sin, cos */
   PTRIG_FAMILY_CUDAMATH = 5,    /* ptrig_cudamath_f32 comparison kernels */
   PTRIG_FAMILY_F32_SINCOS = 6,  /* proposed FP32 sincos (two outputs) */
   PTRIG_FAMILY_HALF_SINCOS = 7, /* fp16 sincos */
   PTRIG_FAMILY_BF16_SINCOS = 8, /* bf16 sincos */
-  PTRIG_FAMILY_COUNT = 9
+  PTRIG_FAMILY_HALF_TAN = 9,    /* fp16 tan */
+  PTRIG_FAMILY_BF16_TAN = 10,   /* bf16 tan */
+  PTRIG_FAMILY_COUNT = 11
 } ptrig_family;
 
 /* Threads per block (64..512, multiple of 32), loads kept in flight per

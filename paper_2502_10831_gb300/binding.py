@@ -19,7 +19,8 @@ LIB_PATH = os.path.join(_PKG, "_build", "libptrig.so")
 SIN, COS, TAN, SINCOS = 0, 1, 2, 3
 FAMILY_F32, FAMILY_HALF, FAMILY_TAYLOR, FAMILY_BWD, FAMILY_BF16, FAMILY_CUDAMATH = 0, 1, 2, 3, 4, 5
 FAMILY_F32_SINCOS, FAMILY_HALF_SINCOS, FAMILY_BF16_SINCOS = 6, 7, 8
-FAMILY_COUNT = 9
+FAMILY_HALF_TAN, FAMILY_BF16_TAN = 9, 10
+FAMILY_COUNT = 11
 BATCH_GRAPH = 1
 
 _P = ctypes.c_void_p

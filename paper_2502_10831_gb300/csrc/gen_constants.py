@@ -116,6 +116,13 @@ def main() -> str:
     w(f"#define PTRIG_PIO2_F1 {lit32(float(p1))}")
     w(f"#define PTRIG_PIO2_F2 {lit32(float(p2))}")
     w(f"#define PTRIG_PIO2_F3 {lit32(float(p3))}")
+    # two pieces for |x| < 2^16 (fp16 storage): P1 and the rest rounded to
+    # nearest; the dropped tail is below 2^-48, so |j| < 2^16 gives at most
+    # 2^-32 on top of the one rounding of the second FMA
+    p2r = _round_bits(HALF_PI - p1, 24)
+    assert abs(HALF_PI - p1 - p2r) <= Fraction(1, 2 ** 48)
+    w("/* pi/2 = PIO2_F1 + PIO2_F2R (+ < 2^-48): the two-piece split for |x| < 2^16 */")
+    w(f"#define PTRIG_PIO2_F2R {lit32(float(p2r))}")
     w(f"#define PTRIG_2_OVER_PI_F {lit32(f32(2 / PI))}")
     w(f"#define PTRIG_12_OVER_PI_F {lit32(f32(12 / PI))}")
     w(f"#define PTRIG_PIO2_F {lit32(f32(HALF_PI))}")

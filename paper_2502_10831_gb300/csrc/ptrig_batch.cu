@@ -142,7 +142,7 @@ static __device__ __noinline__ void batch_tile(const ptrig_desc d, uint64_t star
 // otherwise and for the len % 4 tail; out-of-line full reduction after an
 // angle beyond the FP32 reduction range, as in the elementwise kernels.
 template <int OP>
-__device__ __forceinline__ void batch_block(const BatchTile &t, const STab *s_tab) {
+__device__ __forceinline__ void batch_block(const BatchTile &t, STab *s_tab) {
   using F = Proposed<OP>;
   float *y1 = (OP == OP_SINCOS) ? t.y1 : nullptr;
   uintptr_t a = (uintptr_t)t.x | (uintptr_t)t.y0;
@@ -156,6 +156,10 @@ __device__ __forceinline__ void batch_block(const BatchTile &t, const STab *s_ta
     const uint32_t i = threadIdx.x + r * blockDim.x;
     if (i < nv) buf[r] = ld_stream(xv + i);
   }
+  // the table is staged while the first loads are in flight (the selector is
+  // uniform over the block, so every thread reaches this barrier)
+  stage_stab(s_tab);
+  __syncthreads();
   uint32_t resume = 0;
   for (uint32_t v0 = threadIdx.x; v0 < nv; v0 += R * blockDim.x) {
 #pragma unroll
@@ -185,10 +189,8 @@ tail:
 __global__ void __launch_bounds__(512) k_batch_tiles(const BatchTile *__restrict__ tiles, uint32_t end_sin,
                                                      uint32_t end_cos, uint32_t end_tan) {
   __shared__ STab s_tab;
-  stage_stab(&s_tab);
   const uint32_t b = blockIdx.x;
   const BatchTile t = tiles[b];
-  __syncthreads();
   if (b < end_sin)
     batch_block<OP_SIN>(t, &s_tab);
   else if (b < end_cos)

@@ -39,14 +39,7 @@ static __device__ __noinline__ void bwd_resume_full(const float *__restrict__ x,
 template <int OP, int D, bool PERSIST>
 __global__ void __launch_bounds__(512) k_bwd(const float *__restrict__ x, const float *gy, float *gx, size_t n) {
   __shared__ float4 s_tab[8];
-  if (threadIdx.x < 8) s_tab[threadIdx.x] = c_tab_f32[threadIdx.x];
-  __syncthreads();
   const size_t nvec = n / 4;
-  if (blockIdx.x == 0) {
-    for (size_t k = nvec * 4 + threadIdx.x; k < n; k += blockDim.x) {
-      gx[k] = __fmul_rn(gy[k], Deriv<OP>::template eval<true>(x[k], s_tab));
-    }
-  }
   size_t i, step, end;
   if (PERSIST) {
     i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -63,12 +56,21 @@ __global__ void __launch_bounds__(512) k_bwd(const float *__restrict__ x, const 
   const uint4 *gv = reinterpret_cast<const uint4 *>(gy);
   size_t resume = 0;
   uint4 bx[D], bg[D];
+  // the first loads go out before the table is staged (the barrier then waits
+  // while they are in flight)
 #pragma unroll
   for (int d = 0; d < D; ++d) {
     const size_t j = i + (size_t)d * step;
     if (j < end) {
       bx[d] = ld_stream(xv + j);
       bg[d] = gv[j];
+    }
+  }
+  if (threadIdx.x < 8) s_tab[threadIdx.x] = c_tab_f32[threadIdx.x];
+  __syncthreads();
+  if (blockIdx.x == 0) {
+    for (size_t k = nvec * 4 + threadIdx.x; k < n; k += blockDim.x) {
+      gx[k] = __fmul_rn(gy[k], Deriv<OP>::template eval<true>(x[k], s_tab));
     }
   }
   for (; i < end; i += (size_t)D * step) {
@@ -288,8 +290,6 @@ __global__ void __launch_bounds__(256) k_loss(const float *__restrict__ x, const
   constexpr int D = 2;
   __shared__ float4 s_tab[8];
   __shared__ double s_sum[8];
-  if (threadIdx.x < 8) s_tab[threadIdx.x] = c_tab_f32[threadIdx.x];
-  __syncthreads();
   FSum fast;
   double acc = 0.0;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
@@ -304,6 +304,8 @@ __global__ void __launch_bounds__(256) k_loss(const float *__restrict__ x, const
     const size_t j = i + (size_t)d * stride;
     if (j < nvec) buf[d] = load_loss_vec(x, w, v, u, j);
   }
+  if (threadIdx.x < 8) s_tab[threadIdx.x] = c_tab_f32[threadIdx.x];  // after the first loads
+  __syncthreads();
   for (; i < nvec; i += (size_t)D * stride) {
 #pragma unroll
     for (int d = 0; d < D; ++d) {

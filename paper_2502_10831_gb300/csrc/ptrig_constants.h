@@ -7,6 +7,8 @@
 #define PTRIG_PIO2_F1 0x1.921fb40000000p+0f
 #define PTRIG_PIO2_F2 0x1.4442d00000000p-24f
 #define PTRIG_PIO2_F3 0x1.84698a0000000p-48f
+/* pi/2 = PIO2_F1 + PIO2_F2R (+ < 2^-48): the two-piece split for |x| < 2^16 */
+#define PTRIG_PIO2_F2R 0x1.4442d20000000p-24f
 #define PTRIG_2_OVER_PI_F 0x1.45f3060000000p-1f
 #define PTRIG_12_OVER_PI_F 0x1.e8ec8a0000000p+1f
 #define PTRIG_PIO2_F 0x1.921fb60000000p+0f

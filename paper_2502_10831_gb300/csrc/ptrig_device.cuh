@@ -122,6 +122,17 @@ __device__ __forceinline__ RedF reduce_fast(float x) {
   return {r, __float_as_uint(y)};
 }
 
+// The same reduction with two pieces, for |x| < 2^16 (fp16 storage):
+// PIO2_F1 + PIO2_F2R leaves a tail below 2^-48, so with |j| < 2^16 the
+// result carries at most 2^-32 beyond the second FMA's one rounding.
+__device__ __forceinline__ RedF reduce_fast_2p(float x) {
+  const float y = __fmaf_rn(x, PTRIG_2_OVER_PI_F, PTRIG_RINT_MAGIC_F);
+  const float jf = __fsub_rn(y, PTRIG_RINT_MAGIC_F);
+  float r = __fmaf_rn(-jf, PTRIG_PIO2_F1, x);
+  r = __fmaf_rn(-jf, PTRIG_PIO2_F2R, r);
+  return {r, __float_as_uint(y)};
+}
+
 // Two angles at once with packed FP32 (FFMA2 / FADD2): the same roundings,
 // lane by lane, as reduce_fast().
 struct RedF2 {
@@ -337,15 +348,20 @@ __device__ __forceinline__ float2 seg_nd(const STab *tab, uint32_t code, float r
 // m0 (and m1 for sincos) are the lanes' values without the quadrant sign of
 // sin and cos; code0 / code1 carry it in bit 4 (tan needs none: the rows fold
 // its sign into D).
-template <int OP>
+// TWO: the two-piece reduction (|x| < 2^16, fp16 storage).
+template <int OP, bool TWO>
 __device__ __forceinline__ void proposed_pair(float2 x, const STab *tab, float2 &m0, float2 &m1, uint32_t &code0,
                                               uint32_t &code1) {
   const float2 y = __ffma2_rn(x, make_float2(PTRIG_2_OVER_PI_F, PTRIG_2_OVER_PI_F),
                               make_float2(PTRIG_RINT_MAGIC_F, PTRIG_RINT_MAGIC_F));
   const float2 jf = __fadd2_rn(y, make_float2(-PTRIG_RINT_MAGIC_F, -PTRIG_RINT_MAGIC_F));
   float2 r = __ffma2_rn(jf, make_float2(-PTRIG_PIO2_F1, -PTRIG_PIO2_F1), x);
-  r = __ffma2_rn(jf, make_float2(-PTRIG_PIO2_F2, -PTRIG_PIO2_F2), r);
-  r = __ffma2_rn(jf, make_float2(-PTRIG_PIO2_F3, -PTRIG_PIO2_F3), r);
+  if (TWO) {
+    r = __ffma2_rn(jf, make_float2(-PTRIG_PIO2_F2R, -PTRIG_PIO2_F2R), r);
+  } else {
+    r = __ffma2_rn(jf, make_float2(-PTRIG_PIO2_F2, -PTRIG_PIO2_F2), r);
+    r = __ffma2_rn(jf, make_float2(-PTRIG_PIO2_F3, -PTRIG_PIO2_F3), r);
+  }
   const float2 v = seg_code2(r, y);
   code0 = __float_as_uint(v.x);
   code1 = __float_as_uint(v.y);
@@ -364,12 +380,12 @@ __device__ __forceinline__ void proposed_pair(float2 x, const STab *tab, float2 
   }
 }
 
-// FP32 reduction with the side path above lim.
-template <bool FULL>
+// FP32 reduction with the side path above lim; TWO: the two-piece fast
+// reduction (the caller guarantees that finite inputs lie below 2^16).
+template <bool FULL, bool TWO = false>
 __device__ __forceinline__ RedF reduce_sel(float x, float lim = PTRIG_FAST_LIMIT_F) {
-  if (!FULL) return reduce_fast(x);
-  RedF red = reduce_fast(x);
-  if (__builtin_expect(!(fabsf(x) <= lim), 0)) red = reduce_slow_f32(x);
+  RedF red = TWO ? reduce_fast_2p(x) : reduce_fast(x);
+  if (FULL && __builtin_expect(!(fabsf(x) <= lim), 0)) red = reduce_slow_f32(x);
   return red;
 }
 
@@ -386,13 +402,14 @@ struct Proposed {
   static constexpr int GROUP = 1;           // 16-byte accesses
   // The FP32 reduction bound of the signed-row index.
   __device__ __forceinline__ static float limit() { return PTRIG_SEG_LIMIT_F; }
+  template <bool TWO = false>
   __device__ __forceinline__ static void eval_pair(float2 x, const STab *tab, float2 &m0, float2 &m1,
                                                    uint32_t &c0, uint32_t &c1) {
-    proposed_pair<OP>(x, tab, m0, m1, c0, c1);
+    proposed_pair<OP, TWO>(x, tab, m0, m1, c0, c1);
   }
-  template <bool FULL = true>
+  template <bool FULL = true, bool TWO = false>
   __device__ __forceinline__ static void eval(float x, const STab *tab, float &o0, float &o1) {
-    const RedF red = reduce_sel<FULL>(x, PTRIG_SEG_LIMIT_F);
+    const RedF red = reduce_sel<FULL, TWO>(x, PTRIG_SEG_LIMIT_F);
     const uint32_t code = seg_code(red.r, red.jb);
     const float2 nd = seg_nd(tab, code, red.r);
     if (OP == OP_TAN) {
@@ -428,9 +445,10 @@ struct Taylor {
   static constexpr bool SIGNED_OUT = false;
   static constexpr int GROUP = 2;  // 32-byte accesses
   __device__ __forceinline__ static float limit() { return PTRIG_FAST_LIMIT_F; }
+  template <bool TWO = false>
   __device__ __forceinline__ static void eval_pair(float2, const STab *, float2 &, float2 &, uint32_t &,
                                                    uint32_t &) {}
-  template <bool FULL = true>
+  template <bool FULL = true, bool TWO = false>
   __device__ __forceinline__ static void eval(float x, const STab *, float &o0, float &) {
     const RedF red = reduce_sel<FULL>(x);
     const float t = fabsf(red.r);
@@ -536,6 +554,7 @@ template <>
 struct Storage<float> {
   static constexpr int EPV = 4;  // elements per 16-byte vector
   static constexpr bool RANGE_CHECK = true;
+  static constexpr bool TWO_PIECE = false;
   __device__ __forceinline__ static void unpack(const uint4 &v, float (&f)[4]) {
     f[0] = __uint_as_float(v.x);
     f[1] = __uint_as_float(v.y);
@@ -554,6 +573,7 @@ template <>
 struct Storage<__half> {
   static constexpr int EPV = 8;
   static constexpr bool RANGE_CHECK = false;  // |x| <= 65504 < 2^19, or inf / NaN
+  static constexpr bool TWO_PIECE = true;     // |x| < 2^16: two pieces of pi/2 suffice
   __device__ __forceinline__ static float2 to_float2(uint32_t w) {
     __half2 h;
     *reinterpret_cast<uint32_t *>(&h) = w;
@@ -591,6 +611,7 @@ template <>
 struct Storage<__nv_bfloat16> {
   static constexpr int EPV = 8;
   static constexpr bool RANGE_CHECK = true;
+  static constexpr bool TWO_PIECE = false;
   __device__ __forceinline__ static float2 to_float2(uint32_t w) {
     __nv_bfloat162 h;
     *reinterpret_cast<uint32_t *>(&h) = w;

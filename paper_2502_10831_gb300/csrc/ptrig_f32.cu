@@ -58,9 +58,10 @@ struct CudaMath {
   static constexpr bool SIGNED_OUT = false;
   static constexpr int GROUP = 2;
   __device__ __forceinline__ static float limit() { return PTRIG_FAST_LIMIT_F; }
+  template <bool TWO = false>
   __device__ __forceinline__ static void eval_pair(float2, const STab *, float2 &, float2 &, uint32_t &,
                                                    uint32_t &) {}
-  template <bool FULL = true>
+  template <bool FULL = true, bool TWO = false>
   __device__ __forceinline__ static void eval(float x, const STab *, float &o0, float &o1) {
     if (FAST) {
       if (OP == OP_SIN) o0 = __sinf(x);

@@ -6,7 +6,7 @@
 
 namespace ptrig {
 
-template <typename T, int FAMILY, int FAMILY_SINCOS>
+template <typename T, int FAMILY, int FAMILY_TAN, int FAMILY_SINCOS>
 static ptrig_status launch_half(int op, const void *x, void *y0, void *y1, size_t n, cudaStream_t s) {
   const T *xi = static_cast<const T *>(x);
   T *o0 = static_cast<T *>(y0);
@@ -17,7 +17,7 @@ static ptrig_status launch_half(int op, const void *x, void *y0, void *y1, size_
     case OP_COS:
       return launch_map<T, Proposed<OP_COS>>(FAMILY, xi, o0, o1, n, s);
     case OP_TAN:
-      return launch_map<T, Proposed<OP_TAN>>(FAMILY, xi, o0, o1, n, s);
+      return launch_map<T, Proposed<OP_TAN>>(FAMILY_TAN, xi, o0, o1, n, s);
     case OP_SINCOS:
       return launch_map<T, Proposed<OP_SINCOS>>(FAMILY_SINCOS, xi, o0, o1, n, s);
     default:
@@ -26,11 +26,12 @@ static ptrig_status launch_half(int op, const void *x, void *y0, void *y1, size_
 }
 
 ptrig_status launch_proposed_f16(int op, const void *x, void *y0, void *y1, size_t n, cudaStream_t s) {
-  return launch_half<__half, PTRIG_FAMILY_HALF, PTRIG_FAMILY_HALF_SINCOS>(op, x, y0, y1, n, s);
+  return launch_half<__half, PTRIG_FAMILY_HALF, PTRIG_FAMILY_HALF_TAN, PTRIG_FAMILY_HALF_SINCOS>(op, x, y0, y1, n, s);
 }
 
 ptrig_status launch_proposed_bf16(int op, const void *x, void *y0, void *y1, size_t n, cudaStream_t s) {
-  return launch_half<__nv_bfloat16, PTRIG_FAMILY_BF16, PTRIG_FAMILY_BF16_SINCOS>(op, x, y0, y1, n, s);
+  return launch_half<__nv_bfloat16, PTRIG_FAMILY_BF16, PTRIG_FAMILY_BF16_TAN, PTRIG_FAMILY_BF16_SINCOS>(op, x, y0, y1,
+                                                                                                     n, s);
 }
 
 }  // namespace ptrig

@@ -9,6 +9,7 @@
 #pragma once
 
 #include <climits>
+#include <type_traits>
 
 #include "ptrig_device.cuh"
 #include "ptrig_internal.h"
@@ -32,8 +33,7 @@ __device__ __forceinline__ bool group_fast(const float (&f)[E]) {
 // false, storing nothing, when an element lies outside the FP32 reduction
 // range (or every element is NaN, or one is infinite); the caller then hands
 // the rest of its work to the full-reduction path.  The pair forms evaluate
-// first and check the largest |x| of the vector before the store, so that
-// each pair is unpacked only when it is computed.
+// first and check the largest |x| of the vector just before the store.
 // 16-bit storage with the pair form: lanes stay in float2 from the packed
 // input word to the packed output word; the quadrant signs of sin and cos
 // (bit 4 of each lane's row code) are gathered into bits 15 and 31 with one
@@ -45,15 +45,19 @@ template <typename T, class F>
 __device__ __forceinline__ bool map_vector_fast_h(uint4 v, size_t i, T *y0, T *y1, const STab *tab) {
   using S = Storage<T>;
   const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+  // all four words unpacked first, so the conversions overlap
+  float2 fv[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) fv[k] = S::to_float2(w[k]);
   uint32_t a[4], b[4];
   float m = 0.0f;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const float2 f = S::to_float2(w[k]);
+    const float2 f = fv[k];
     if constexpr (S::RANGE_CHECK) m = fmaxf(m, fmaxf(fabsf(f.x), fabsf(f.y)));
     float2 m0, m1;
     uint32_t c0, c1;
-    F::eval_pair(f, tab, m0, m1, c0, c1);
+    F::template eval_pair<S::TWO_PIECE>(f, tab, m0, m1, c0, c1);
     uint32_t sg = 0;
     if constexpr (F::SIGNED_OUT) sg = (__byte_perm(c0, c1, 0x4000) << 3) & 0x80008000u;
     a[k] = S::from_float2(m0) ^ sg;
@@ -112,7 +116,7 @@ __device__ __forceinline__ bool map_vector_fast(uint4 v, size_t i, T *y0, T *y1,
     if (!group_fast<F, E>(f)) return false;
   }
 #pragma unroll
-  for (int e = 0; e < E; ++e) F::template eval<false>(f[e], tab, o0[e], o1[e]);
+  for (int e = 0; e < E; ++e) F::template eval<false, S::TWO_PIECE>(f[e], tab, o0[e], o1[e]);
   st_stream(reinterpret_cast<uint4 *>(y0) + i, S::pack(o0));
   if constexpr (F::NOUT == 2) st_stream(reinterpret_cast<uint4 *>(y1) + i, S::pack(o1));
   return true;
@@ -131,7 +135,7 @@ static __device__ __noinline__ void map_resume_full(const T *__restrict__ x, T *
   for (; i < nvec; i += stride) {
     float f[E], o0[E], o1[E];
     S::unpack(ld_stream(reinterpret_cast<const uint4 *>(x) + i), f);
-    for (int e = 0; e < E; ++e) F::template eval<true>(f[e], tab, o0[e], o1[e]);
+    for (int e = 0; e < E; ++e) F::template eval<true, S::TWO_PIECE>(f[e], tab, o0[e], o1[e]);
     st_stream(reinterpret_cast<uint4 *>(y0) + i, S::pack(o0));
     if constexpr (F::NOUT == 2) st_stream(reinterpret_cast<uint4 *>(y1) + i, S::pack(o1));
   }
@@ -206,19 +210,9 @@ template <typename T, class F, int D, bool PERSIST>
 __device__ __forceinline__ void map_stream(const T *__restrict__ x, T *__restrict__ y0, T *__restrict__ y1,
                                            size_t n) {
   __shared__ STab s_tab;
-  stage_stab(&s_tab);
-  __syncthreads();
   using S = Storage<T>;
   constexpr int E = S::EPV;
   const size_t nvec = n / E;
-  if (blockIdx.x == 0) {  // the n % E elements after the last whole vector
-    for (size_t k = nvec * E + threadIdx.x; k < n; k += blockDim.x) {
-      float o0, o1;
-      F::template eval<true>(S::load1(x + k), &s_tab, o0, o1);
-      S::store1(y0 + k, o0);
-      if constexpr (F::NOUT == 2) S::store1(y1 + k, o1);
-    }
-  }
   size_t i, step, end;
   if (PERSIST) {
     i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -233,11 +227,23 @@ __device__ __forceinline__ void map_stream(const T *__restrict__ x, T *__restric
   }
   const uint4 *xv = reinterpret_cast<const uint4 *>(x);
   size_t resume = 0;
+  // The first D loads go out before the table is staged: the barrier below
+  // then waits while they are in flight instead of in front of them.
   uint4 buf[D];
 #pragma unroll
   for (int d = 0; d < D; ++d) {
     const size_t j = i + (size_t)d * step;
     if (j < end) buf[d] = ld_stream(xv + j);
+  }
+  stage_stab(&s_tab);
+  __syncthreads();
+  if (blockIdx.x == 0) {  // the n % E elements after the last whole vector
+    for (size_t k = nvec * E + threadIdx.x; k < n; k += blockDim.x) {
+      float o0, o1;
+      F::template eval<true, S::TWO_PIECE>(S::load1(x + k), &s_tab, o0, o1);
+      S::store1(y0 + k, o0);
+      if constexpr (F::NOUT == 2) S::store1(y1 + k, o1);
+    }
   }
   for (; i < end; i += (size_t)D * step) {
 #pragma unroll
@@ -336,11 +342,9 @@ __global__ void __launch_bounds__(512) k_map(const T *__restrict__ x, T *__restr
     map_stream<T, F, D, PERSIST>(x, y0, y1, n);
 }
 
-// Single-output functions on 16-bit storage are instruction-bound: this
-// instance caps their registers at 64 (two 512-thread blocks per SM) for more
-// resident warps.  FP32 is memory-bound and sincos would spill, so both keep
-// k_map; on GB300 even a minimum of one block per SM in the launch bounds
-// slowed the FP32 kernels by 5-10% at the same register count.
+// Single-output functions on bf16 storage run faster with their registers
+// capped at 64 (two 512-thread blocks per SM, more resident warps); fp16,
+// FP32 and sincos measured faster without the cap.
 template <typename T, class F, int D, bool PERSIST, int W>
 __global__ void __launch_bounds__(512, 2) k_map_capped(const T *__restrict__ x, T *__restrict__ y0,
                                                        T *__restrict__ y1, size_t n) {
@@ -351,7 +355,7 @@ __global__ void __launch_bounds__(512, 2) k_map_capped(const T *__restrict__ x, 
 }
 
 template <typename T, class F>
-constexpr bool map_capped() { return sizeof(T) == 2 && F::NOUT == 1; }
+constexpr bool map_capped() { return std::is_same<T, __nv_bfloat16>::value && F::NOUT == 1; }
 
 template <typename T, class F, int D, bool PERSIST, int W>
 void launch_k_map(unsigned grid, int block, cudaStream_t s, const T *x, T *y0, T *y1, size_t n) {
@@ -371,7 +375,7 @@ __global__ void __launch_bounds__(512) k_map_scalar(const T *__restrict__ x, T *
   using S = Storage<T>;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)blockDim.x * gridDim.x) {
     float o0, o1;
-    F::template eval<true>(S::load1(x + i), &s_tab, o0, o1);
+    F::template eval<true, S::TWO_PIECE>(S::load1(x + i), &s_tab, o0, o1);
     S::store1(y0 + i, o0);
     if constexpr (F::NOUT == 2) S::store1(y1 + i, o1);
   }
@@ -388,9 +392,53 @@ inline size_t grid_for(size_t units, size_t per_block, const LaunchCfg &c, int s
   return blocks;
 }
 
+// One-shot blocks of 64 threads over whole chunks: block b streams the 16-byte
+// vectors [64 D b, 64 D (b + 1)) with no bounds checks and addresses at fixed
+// offsets from one base, which keeps the kernel at about two thirds of
+// k_map's registers.  The D loads of a thread go out before the table is
+// staged, so the barrier waits while they are in flight.  An angle beyond
+// the FP32 reduction range hands the thread's remaining vectors of the chunk
+// to map_resume_full.  The partial last chunk and the n % E tail go to k_map.
+template <typename T, class F, int D>
+__device__ __forceinline__ void map_chunk64(const T *__restrict__ x, T *__restrict__ y0, T *__restrict__ y1) {
+  constexpr uint32_t B = 64;
+  __shared__ STab s_tab;
+  const size_t base = (size_t)blockIdx.x * (B * D) + threadIdx.x;
+  const uint4 *xp = reinterpret_cast<const uint4 *>(x) + base;
+  T *yb0 = reinterpret_cast<T *>(reinterpret_cast<uint4 *>(y0) + base);
+  T *yb1 = (F::NOUT == 2) ? reinterpret_cast<T *>(reinterpret_cast<uint4 *>(y1) + base) : y1;
+  uint4 buf[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) buf[d] = ld_stream(xp + d * B);
+  stage_stab(&s_tab);
+  __syncthreads();
+  size_t resume = 0;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    if (!map_vector_fast<T, F>(buf[d], (size_t)d * B, yb0, yb1, &s_tab)) {
+      resume = base + (size_t)d * B + 1;  // +1 so that 0 means "finished"
+      goto full;
+    }
+  }
+  return;
+full:
+  map_resume_full<T, F>(x, y0, y1, resume - 1, base + B * D, B, &s_tab);
+}
+
+template <typename T, class F, int D>
+__global__ void __launch_bounds__(64) k_chunk64(const T *__restrict__ x, T *__restrict__ y0, T *__restrict__ y1) {
+  map_chunk64<T, F, D>(x, y0, y1);
+}
+
+template <typename T, class F, int D>
+__global__ void __launch_bounds__(64, 16) k_chunk64_capped(const T *__restrict__ x, T *__restrict__ y0,
+                                                           T *__restrict__ y1) {
+  map_chunk64<T, F, D>(x, y0, y1);
+}
+
 template <typename T, class F, int D, int W>
 ptrig_status launch_map_w(const LaunchCfg &c, int sms, const T *x, T *y0, T *y1, size_t n, cudaStream_t s) {
-  const size_t nvec = n / (Storage<T>::EPV * W);  // groups of W vectors
+  size_t nvec = n / (Storage<T>::EPV * W);  // groups of W vectors
   // one-shot needs one block per chunk; beyond the grid limit the persistent
   // grid (8 blocks per SM) walks the array instead
   const bool oneshot = c.blocks_per_sm == 0 && (nvec + (size_t)c.block * D - 1) / ((size_t)c.block * D) <= INT_MAX;
@@ -401,6 +449,26 @@ ptrig_status launch_map_w(const LaunchCfg &c, int sms, const T *x, T *y0, T *y1,
     if (g < 1) g = 1;
     launch_k_map<T, F, D, true, W>((unsigned)g, c.block, s, x, y0, y1, n);
   } else {  // one-shot: one contiguous chunk of D * block groups per block
+    if constexpr (W == 1 && F::USES_TABLE) {
+      if (c.block == 64) {  // whole chunks in k_chunk64, the rest in k_map
+        const size_t nfull = nvec / (64 * D);
+        if (nfull > 0) {
+          if constexpr (map_capped<T, F>())
+            k_chunk64_capped<T, F, D><<<(unsigned)nfull, 64, 0, s>>>(x, y0, y1);
+          else
+            k_chunk64<T, F, D><<<(unsigned)nfull, 64, 0, s>>>(x, y0, y1);
+          const ptrig_status st = finish_launch();
+          if (st != PTRIG_OK) return st;
+        }
+        const size_t done = nfull * 64 * D * Storage<T>::EPV;
+        if (done == n) return PTRIG_OK;
+        x += done;
+        y0 += done;
+        if (F::NOUT == 2) y1 += done;
+        n -= done;
+        nvec -= nfull * 64 * D;
+      }
+    }
     const size_t g = grid_for(nvec, (size_t)c.block * D, LaunchCfg{c.block, D, 0}, sms);
     launch_k_map<T, F, D, false, W>((unsigned)g, c.block, s, x, y0, y1, n);
   }

@@ -68,7 +68,7 @@ def test_host_validation_without_gpu(lib):
     assert lib.ptrig_cudamath_f32(4, 0, 1024, 2048, None, 4, None) == 1
     assert lib.ptrig_set_launch_config(0, 100, 4, 0) == 1
     assert lib.ptrig_set_launch_config(0, 256, 3, 0) == 1
-    assert lib.ptrig_set_launch_config(9, 256, 4, 0) == 1
+    assert lib.ptrig_set_launch_config(11, 256, 4, 0) == 1
     assert lib.ptrig_set_launch_config(0, 256, 16, 0) == 1
     assert lib.ptrig_fp64_fma_probe(1024, 300, 10, None) == 1  # not a multiple of 256
     assert lib.ptrig_fp64_fma_probe(1024, 512, 0, None) == 1
@@ -86,12 +86,14 @@ def test_launch_config_roundtrip(lib):
 
 def test_default_launch_configs(lib):
     """The per-family defaults picked by the GB300 sweeps: one-shot 64-thread
-    blocks, eight 16-byte loads in flight for fp16, two for the FP32 sincos,
-    four otherwise; the CUDA-math comparison kernels persistent."""
+    blocks (the whole-chunk kernel) with four 16-byte loads in flight, eight
+    for fp16 / bf16 tan, 128-thread blocks for the fp16 sincos; the CUDA-math
+    comparison kernels persistent."""
     from paper_2502_10831_gb300 import binding as B
-    want = {B.FAMILY_F32: (64, 4, 0), B.FAMILY_HALF: (64, 8, 0), B.FAMILY_TAYLOR: (64, 4, 0),
+    want = {B.FAMILY_F32: (64, 4, 0), B.FAMILY_HALF: (64, 4, 0), B.FAMILY_TAYLOR: (64, 4, 0),
             B.FAMILY_BWD: (64, 4, 0), B.FAMILY_BF16: (64, 4, 0), B.FAMILY_CUDAMATH: (512, 2, 8),
-            B.FAMILY_F32_SINCOS: (64, 2, 0), B.FAMILY_HALF_SINCOS: (64, 8, 0), B.FAMILY_BF16_SINCOS: (64, 4, 0)}
+            B.FAMILY_F32_SINCOS: (64, 4, 0), B.FAMILY_HALF_SINCOS: (128, 4, 0), B.FAMILY_BF16_SINCOS: (64, 4, 0),
+            B.FAMILY_HALF_TAN: (64, 8, 0), B.FAMILY_BF16_TAN: (64, 8, 0)}
     assert len(want) == B.FAMILY_COUNT
     for fam, cfg in want.items():
         assert B.ptrig_get_launch_config(fam) == cfg, fam

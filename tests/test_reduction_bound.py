@@ -51,3 +51,47 @@ def test_no_float_closer_than_bound_to_half_pi_multiple(oracle):
     assert np.log2(d.min()) > -27.9
     # relative error of r at the closest float stays below 2^-21.2
     assert 2.0 ** -23 + 2.0 ** -49.65 / d.min() < 2.0 ** -21.2
+
+
+def _rn32(v):
+    """v rounded to the nearest FP32 (ties to even), exactly (normal range)."""
+    if v == 0:
+        return Fraction(0)
+    s = -1 if v < 0 else 1
+    a = abs(v)
+    e = a.numerator.bit_length() - a.denominator.bit_length()
+    if Fraction(2) ** e > a:
+        e -= 1
+    sc = Fraction(2) ** (23 - e)
+    m = a * sc
+    fl = m.numerator // m.denominator
+    rem = m - fl
+    if rem > Fraction(1, 2) or (rem == Fraction(1, 2) and fl % 2):
+        fl += 1
+    return s * Fraction(fl) / sc
+
+
+def test_two_piece_reduction_for_fp16_storage():
+    """fp16 storage reduces with two pieces of pi/2 (|x| < 2^16): over every
+    finite nonzero fp16 value, emulated exactly, the two-piece r stays within
+    2^-21 (relative) of the three-piece r and selects the same signed row,
+    so the FP32 segment dump describes the fp16 kernels too."""
+    c = {n: Fraction(_const(n)) for n in ("PTRIG_PIO2_F1", "PTRIG_PIO2_F2", "PTRIG_PIO2_F3", "PTRIG_PIO2_F2R",
+                                          "PTRIG_2_OVER_PI_F", "PTRIG_12_OVER_PI_F", "PTRIG_RINT_MAGIC_F")}
+    M = c["PTRIG_RINT_MAGIC_F"]
+    bits = np.arange(1 << 16, dtype=np.uint32).astype(np.uint16)
+    with np.errstate(invalid="ignore"):
+        xs = bits.view(np.float16).astype(np.float64)
+    worst = Fraction(0)
+    for xv in xs[np.isfinite(xs) & (xs != 0)]:
+        x = Fraction(float(xv))
+        y = _rn32(x * c["PTRIG_2_OVER_PI_F"] + M)
+        jf = y - M
+        r1 = _rn32(x - jf * c["PTRIG_PIO2_F1"])  # exact
+        r3 = _rn32(_rn32(r1 - jf * c["PTRIG_PIO2_F2"]) - jf * c["PTRIG_PIO2_F3"])
+        r2 = _rn32(r1 - jf * c["PTRIG_PIO2_F2R"])
+        base = M + 8 * jf
+        assert math.floor(base + r3 * c["PTRIG_12_OVER_PI_F"]) == math.floor(base + r2 * c["PTRIG_12_OVER_PI_F"]), xv
+        if r3 != 0 and jf != 0:
+            worst = max(worst, abs(r2 - r3) / abs(r3))
+    assert worst < Fraction(1, 2 ** 21)
