@@ -78,19 +78,24 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append((time.perf_counter(), line.strip()))
 
-    def stop(self, t0=None, t1=None):
-        """Summary of the samples taken between t0 and t1 (perf_counter)."""
+    def stop(self):
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.thread.join(timeout=2)
+
+    def window(self, t0=None, t1=None):
+        """Summary of the samples taken between t0 and t1 (perf_counter)."""
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.12)  # let the sampler read past t1
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ts, line in self.lines:
+        for ts, line in list(self.lines):
             if t0 is not None and not (t0 - 0.05 <= ts <= t1 + 0.05):
                 continue
             parts = [p.strip() for p in line.split(",")]
@@ -111,19 +116,12 @@ class ClockSampler:
 # -------------------------------------------------------------- CPU oracle
 
 
-def oracle_rate(x_host, seconds_budget: float = 12.0, threads: int | None = None):
-    """The FP64 oracle, as it stands, over a bounded sample of the same
-    workload: the step's seven functions on the first `m` angles, spread over
-    the host cores with threads (the C calls release the GIL)."""
+def _oracle_pass(O, xd, threads):
+    """The step's seven functions with the oracle over xd on `threads` host
+    threads (the C calls release the GIL); returns seconds."""
     import numpy as np
     from concurrent.futures import ThreadPoolExecutor
 
-    from oracle import ptrig_oracle as O
-
-    O.lib()
-    threads = threads or os.cpu_count() or 1
-    m = min(x_host.size, 1 << 23)
-    xd = x_host[:m].astype(np.float64)
     parts = np.array_split(xd, threads)
 
     def work(part):
@@ -136,26 +134,56 @@ def oracle_rate(x_host, seconds_budget: float = 12.0, threads: int | None = None
         return part.size
 
     t0 = time.perf_counter()
-    with ThreadPoolExecutor(max_workers=threads) as ex:
-        list(ex.map(work, parts))
-    dt = time.perf_counter() - t0
-    evals = 7 * m
-    # one core, and a float64 libm-class implementation (numpy) for context
-    m1 = min(x_host.size, 1 << 20)
-    t0 = time.perf_counter()
-    work(xd[:m1])
-    one = 7 * m1 / (time.perf_counter() - t0) / 1e9
-    t0 = time.perf_counter()
-    np.sin(xd)
-    np.cos(xd)
-    np.tan(xd)
-    lib = 3 * m / (time.perf_counter() - t0) / 1e9
-    return {"value": evals / dt / 1e9, "unit": "Gelem/s", "cores": threads, "kind": "oracle",
-            "sample": f"first {m} angles of the workload x 7 functions (sincos counted once), "
-                      f"{threads} threads, {dt:.2f} s wall",
-            "one_core": {"value": round(one, 5), "sample": f"first {m1} angles x 7 functions, 1 thread"},
-            "numpy_f64_sin_cos_tan_one_core": {"value": round(lib, 4),
-                                               "note": "context: numpy float64 sin/cos/tan, not the method"}}
+    if threads == 1:
+        work(xd)
+    else:
+        with ThreadPoolExecutor(max_workers=threads) as ex:
+            list(ex.map(work, parts))
+    return time.perf_counter() - t0
+
+
+def oracle_rate(x_host, threads: int | None = None, full: bool = True):
+    """The FP64 oracle, as it stands, over bounded samples of the workloads:
+    the step's seven functions on the first 2^24 angles of the bandwidth
+    workload on every host core (`value`), and with `full` also on 2^20 of
+    them on one core, on the 2^20-angle parity workload on every core, and the
+    host C library's double sin / cos / tan on the same 2^24 angles (context:
+    the inbuilt functions the paper compares against)."""
+    import numpy as np
+
+    from oracle import ptrig_oracle as O
+
+    O.lib()
+    threads = threads or os.cpu_count() or 1
+    m = min(x_host.size, 1 << 24)
+    xd = x_host[:m].astype(np.float64)
+    dt = _oracle_pass(O, xd, threads)
+    out = {"value": 7 * m / dt / 1e9, "unit": "Gelem/s", "cores": threads, "kind": "oracle",
+           "sample": f"first {m} angles of the bandwidth workload x 7 functions (sincos counted once), "
+                     f"{threads} threads, {dt:.2f} s wall"}
+    if not full:
+        return out
+    m1 = min(m, 1 << 20)
+    t1 = _oracle_pass(O, xd[:m1], 1)
+    out["one_core"] = {"value": round(7 * m1 / t1 / 1e9, 5), "sample": f"first {m1} angles x 7 functions, 1 thread"}
+    from paper_2502_10831_gb300 import workloads as W
+    xc1 = W.parity(1 << 20).astype(np.float64)
+    tc = _oracle_pass(O, xc1, threads)
+    out["parity_workload"] = {"value": round(7 * xc1.size / tc / 1e9, 5),
+                              "sample": f"the 2^20-angle parity workload x 7 functions, {threads} threads"}
+    try:
+        from cpu_simd import ptrig_cpu as C
+        lib = {}
+        for label, th, xs in (("all_cores", threads, xd), ("one_core", 1, xd[:m1])):
+            t0 = time.perf_counter()
+            for f in ("sin", "cos", "tan"):
+                C.libm(f, xs, th)
+            lib[label] = {"value": round(3 * xs.size / (time.perf_counter() - t0) / 1e9, 4),
+                          "sample": f"{xs.size} angles x sin, cos, tan (C library, double), {th} threads"}
+        out["libm_f64"] = lib
+    except (ImportError, OSError, RuntimeError) as e:
+        out["libm_f64"] = {"unavailable": str(e)}
+    return out
 
 
 def cpu_simd_rate(x_host):
@@ -198,11 +226,11 @@ def run_reference(args, rank, world):
 
     x = W.bandwidth(1 << 22)
     for _ in range(args.warmup):
-        oracle_rate(x[: 1 << 18])
+        oracle_rate(x[: 1 << 18], full=False)
     vals = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        vals.append(oracle_rate(x))
+        vals.append(oracle_rate(x, full=False))
     dt = time.perf_counter() - t0
     v = statistics.median(r["value"] for r in vals)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Gelem/s", "n_gpus": 1,
@@ -357,8 +385,44 @@ def workload_autograd(B, W, torch, dev, rank, log2n):
                       "bwd": {f: bwd_kernel(f) for f in ("sin", "cos", "tan")}}
 
 
+def workload_fp64(B, W, torch, dev, rank, log2n):
+    """The FP64 data path (Sec. 4 evaluates in double) and the paper-faithful
+    FP64 kernels on 2^26 doubles of the bandwidth workload; FP64-issue-bound."""
+    import numpy as np
+    n = 1 << min(log2n, 26)
+    x = torch.from_numpy(W.bandwidth(n, seed=R.shard_seed(W.SEED, rank)).astype(np.float64)).to(dev)
+    y = torch.empty_like(x)
+    s = torch.cuda.current_stream().cuda_stream
+    ks = [Kernel(f"{f}_f64", 16 * n, n, (lambda f=f: getattr(B, f"ptrig_{f}_f64")(x, y, n, s)))
+          for f in ("sin", "cos", "tan")]
+    ks += [Kernel(f"faithful_{f}_f64", 16 * n, n, (lambda fi=fi: B.ptrig_faithful_f64(fi, x, y, n, s)))
+           for fi, f in enumerate(("sin", "cos", "tan"))]
+    meta = {"metric": f"Gelem/s, pi/12 sin/cos/tan in FP64 (proposed and paper-faithful) on 2^{n.bit_length() - 1} "
+                      "doubles", "dtype": "f64",
+            "workload": f"fp64: 2^{n.bit_length() - 1} doubles of the bandwidth mixture; step = FP64 sin, cos, tan and "
+                        "the paper-faithful FP64 sin, cos, tan (one launch each)", "n_per_gpu": n,
+            "l2": "inputs larger than L2 (512 MiB vs 129 MB), no flush"}
+    return ks, meta, {"n": n}
+
+
+def fp64_peak(B, torch, dev, stream):
+    """FP64 FMA throughput of the probe kernel (GFLOP/s, CUDA events)."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sink = torch.empty(sms * 8 * 256, dtype=torch.float64, device=dev)
+    iters = 2048
+    ms = _time_call(lambda: B.ptrig_fp64_fma_probe(sink, iters, sink.numel(), stream.cuda_stream), 5, stream)
+    return sink.numel() * iters * 16 / ms / 1e6, f"ptrig_fp64_fma_probe: {sink.numel()} threads x {iters} x 8 FMA " \
+                                                 "chains, CUDA events"
+
+
+def fp64_flops():
+    """FP64 FLOPs per angle of each FP64 kernel (profiles/fp64_ops.json)."""
+    p = os.path.join(ROOT, "profiles", "fp64_ops.json")
+    return json.load(open(p)).get("kernels", {}) if os.path.exists(p) else {}
+
+
 WORKLOADS = {"bandwidth": workload_bandwidth, "half": workload_half, "large": workload_large,
-             "batch": workload_batch, "autograd": workload_autograd}
+             "batch": workload_batch, "autograd": workload_autograd, "fp64": workload_fp64}
 
 
 def main():
@@ -438,7 +502,7 @@ def main():
     wall = time.perf_counter() - wall0
     if dist:
         dist.barrier()
-    clk = clocks.stop(wall0, wall0 + wall)
+    clk = clocks.window(wall0, wall0 + wall)
     total_ms = R.max_over_ranks(t0.elapsed_time(t1), dist, dev)
     per_kernel_ms = [statistics.mean(ev[s][k].elapsed_time(ev[s][k + 1]) for s in range(args.steps))
                      for k in range(nk)]
@@ -454,21 +518,26 @@ def main():
     dom_i = max(range(nk), key=lambda k: per_kernel_ms[k])
     dom = kernels_list[dom_i]
     achieved = dom.nbytes / (per_kernel_ms[dom_i] * 1e-3) / 1e9
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
-        tr = json.load(open(tpath)).get(dom.name)
-        traffic = tr.get("bytes_per_launch") if isinstance(tr, dict) else tr
+    traffic, traffic_src = lookup_traffic(dom.name, meta["n_per_gpu"], args.workload)
     roofline = {"bound": "hbm", "kernel": dom.name, "achieved": round(achieved, 1), "peak": peak,
                 "peak_kind": "measured (MEASURED_PEAKS.json hbm_gbs, copy)" if peak_kind == "measured" else peak_kind,
                 "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4), "nominal_gbs": NOMINAL_HBM_GBS,
-                "algorithmic_bytes_per_launch": dom.nbytes, "traffic": traffic}
+                "algorithmic_bytes_per_launch": dom.nbytes, "traffic": traffic, "traffic_source": traffic_src}
+    if args.workload == "fp64":  # FP64-issue-bound: the roofline is the FP64 FMA rate
+        pk, how = fp64_peak(B, torch, dev, stream)
+        fl = fp64_flops().get(dom.name, {}).get("flops_per_element")
+        ach = fl * dom.elems / (per_kernel_ms[dom_i] * 1e-3) / 1e9 if fl else None
+        roofline = {"bound": "fp64", "kernel": dom.name, "achieved": round(ach, 1) if ach else None,
+                    "peak": round(pk, 1), "peak_kind": "measured (" + how + ")", "unit": "GFLOP/s",
+                    "frac": round(ach / pk, 4) if ach else None, "flops_per_element": fl,
+                    "flops_source": "profiles/fp64_ops.json", "traffic": None}
     config = {"workload": meta["workload"], "n_per_gpu": meta["n_per_gpu"], "l2": meta["l2"],
               "launch_configs": {name: B.ptrig_get_launch_config(fam) for name, fam in (
                   ("f32", B.FAMILY_F32), ("f32_sincos", B.FAMILY_F32_SINCOS), ("taylor", B.FAMILY_TAYLOR),
                   ("half", B.FAMILY_HALF), ("half_sincos", B.FAMILY_HALF_SINCOS), ("bf16", B.FAMILY_BF16),
-                  ("bf16_sincos", B.FAMILY_BF16_SINCOS), ("bwd", B.FAMILY_BWD))}}
+                  ("bf16_sincos", B.FAMILY_BF16_SINCOS), ("half_tan", B.FAMILY_HALF_TAN),
+                  ("bf16_tan", B.FAMILY_BF16_TAN), ("bwd", B.FAMILY_BWD))}}
     if "autotuned" in meta:
         config["batch_autotuned"] = meta["autotuned"]
     line = {"metric": meta["metric"], "value": round(value, 2), "unit": "Gelem/s", "n_gpus": world,
@@ -506,13 +575,27 @@ def main():
     if args.workload == "large" and rank == 0:
         line["side_paths"] = side_paths(B, torch, dev, stream, peak)
     if args.workload == "bandwidth" and not args.no_extras and rank == 0:
-        line.update(extras(args, B, W, state["x"], state["x_host"], state["n"], stream, peak, kernels))
+        line.update(extras(args, B, W, state, stream, peak, kernels, clocks, rank))
+    clocks.stop()
     if rank == 0:
         print(json.dumps(line))
     if dist:
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def lookup_traffic(kernel, n, workload):
+    """ncu DRAM bytes (read + write) of one launch of `kernel` on `n` angles of
+    `workload`, from profiles/traffic.json; (None, None) when no capture of
+    exactly that launch exists."""
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(tpath):
+        return None, None
+    for e in json.load(open(tpath)).get("captures", []):
+        if e.get("kernel") == kernel and e.get("n") == n and e.get("workload") == workload:
+            return e.get("bytes_per_launch"), e.get("source")
+    return None, None
 
 
 def side_paths(B, torch, dev, stream, peak):
@@ -549,10 +632,158 @@ def _time_call(fn, reps, stream):
     return a.elapsed_time(b) / reps
 
 
-def extras(args, B, W, x, x_host, n, stream, peak, kernels):
+def _timed(fn, stream, clocks, min_s=0.3, max_reps=4000, flush=None):
+    """Average CUDA-event time of fn on `stream` after 3 warm-up calls, over
+    enough calls to fill about min_s seconds (so that the clock sampler sees
+    the window), and the clock summary of that window.  With `flush`, an L2
+    flush runs before every call, outside the timed events."""
+    import torch
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    est = max(a.elapsed_time(b), 1e-3)
+    reps = int(min(max_reps, max(3, min_s * 1e3 / est)))
+    w0 = time.perf_counter()
+    if flush is None:
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+    else:
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for e0, e1 in evs:
+            flush()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = sum(e0.elapsed_time(e1) for e0, e1 in evs) / reps
+    w1 = time.perf_counter()
+    return ms, reps, clocks.window(w0, w1)
+
+
+def leg_large(B, W, torch, dev, stream, peak, clocks):
+    """The precision configuration's large-argument set: 2^24 FP32 angles,
+    |x| log-uniform in [1, 1e5] (64 MiB, under L2: the L2 is flushed before
+    every timed call), the four functions; plus sin on 2^24 angles of each
+    reduction side path."""
+    import numpy as np
+    n = 1 << 24
+    sp = stream.cuda_stream
+    x = torch.from_numpy(W.large(n)).to(dev)
+    y0, y1 = torch.empty_like(x), torch.empty_like(x)
+    scratch = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 256 MiB > L2
+
+    def flush():
+        scratch.fill_(1)
+
+    out = {"n": n, "workload": "2^24 fp32 angles, |x| log-uniform in [1, 1e5], random sign (FP32 reduction)",
+           "l2": "64 MiB arrays, L2 flushed (256 MiB write) before every timed call"}
+    for f, nb in (("sin", 8), ("cos", 8), ("tan", 8), ("sincos", 12)):
+        if f == "sincos":
+            fn = (lambda: B.ptrig_sincos_f32(x, y0, y1, n, sp))
+        else:
+            fn = (lambda f=f: getattr(B, f"ptrig_{f}_f32")(x, y0, n, sp))
+        ms, reps, clk = _timed(fn, stream, clocks, flush=flush)
+        out[f"{f}_f32"] = {"ms": round(ms, 4), "gelem_s": round(n / ms / 1e6, 2),
+                           "hbm_frac": round(nb * n / ms / 1e6 / peak, 4), "reps": reps, "clocks": clk}
+    # the same distribution at 4x the size (256 MiB arrays, above L2, no flush):
+    # the 2^24 launches are short enough for their start-up to show
+    n4 = 1 << 26
+    x4 = torch.from_numpy(W.large(n4)).to(dev)
+    z0, z1 = torch.empty_like(x4), torch.empty_like(x4)
+    big = {"n": n4}
+    for f, nb in (("sin", 8), ("cos", 8), ("tan", 8), ("sincos", 12)):
+        if f == "sincos":
+            fn = (lambda: B.ptrig_sincos_f32(x4, z0, z1, n4, sp))
+        else:
+            fn = (lambda f=f: getattr(B, f"ptrig_{f}_f32")(x4, z0, n4, sp))
+        ms, reps, clk = _timed(fn, stream, clocks)
+        big[f"{f}_f32"] = {"ms": round(ms, 4), "gelem_s": round(n4 / ms / 1e6, 2),
+                           "hbm_frac": round(nb * n4 / ms / 1e6 / peak, 4), "clocks": clk}
+    out["at_2p26"] = big
+    del x4, z0, z1
+    side = {}
+    for name, lo, hi in (("fp64_cody_waite", 19.0, 31.0), ("payne_hanek", 31.0, 127.0)):
+        r = np.random.default_rng(7)
+        xh = (2.0 ** r.uniform(lo, hi, n) * r.choice([-1.0, 1.0], n)).astype(np.float32)
+        x.copy_(torch.from_numpy(xh))
+        ms, reps, clk = _timed(lambda: B.ptrig_sin_f32(x, y0, n, sp), stream, clocks, flush=flush)
+        side[name] = {"range": f"|x| log-uniform in [2^{lo:g}, 2^{hi:g})", "ms": round(ms, 3),
+                      "gelem_s": round(n / ms / 1e6, 2), "clocks": clk}
+    out["side_paths_sin_f32"] = side
+    del x, y0, y1, scratch
+    torch.cuda.empty_cache()
+    return out
+
+
+def leg_batch(B, W, torch, dev, stream, peak, clocks, rank):
+    """The batching configuration: 4096 ragged FP32 arrays with per-array
+    selectors, one graph-captured launch (autotuned tile shape) against one
+    launch per array."""
+    ks, meta, st = workload_batch(B, W, torch, dev, rank, 0)
+    k = ks[0]
+    ms, reps, clk = _timed(k.call, stream, clocks)
+    plan = st["plan"]
+    pms, preps, pclk = _timed(lambda: plan.run_per_array(stream.cuda_stream), stream, clocks, min_s=0.3)
+    total = meta["n_per_gpu"]
+    out = {"arrays": len(st["descs"]), "elements": total, "workload": meta["workload"],
+           "autotuned": meta["autotuned"],
+           "graph": {"ms": round(ms, 4), "gelem_s": round(total / ms / 1e6, 2),
+                     "hbm_frac": round(k.nbytes / ms / 1e6 / peak, 4), "bytes": k.nbytes, "reps": reps,
+                     "clocks": clk},
+           "per_array_launches": {"ms": round(pms, 3), "gelem_s": round(total / pms / 1e6, 2),
+                                  "launches": len(st["descs"]), "reps": preps, "clocks": pclk},
+           "speedup_vs_per_array": round(pms / ms, 2)}
+    plan.close()
+    del ks, st
+    torch.cuda.empty_cache()
+    return out
+
+
+def leg_autograd(B, W, torch, dev, stream, peak, clocks, rank):
+    """The differentiation configuration at [8192, 4096]: the unfused autograd
+    step (sin, cos, tan forward and backward kernels with torch's elementwise
+    ops between them), the fused loss+gradient kernel through autograd and
+    alone, and each derivative kernel."""
+    ks, meta, st = workload_autograd(B, W, torch, dev, rank, 0)
+    nn = st["n"]
+    ums, ureps, uclk = _timed(ks[0].call, stream, clocks)
+    fms, freps, fclk = _timed(st["fused"], stream, clocks)
+    kms, kreps, kclk = _timed(st["fused_kernel"], stream, clocks)
+    out = {"shape": [8192, 4096], "workload": meta["workload"],
+           "unfused_step": {"ms": round(ums, 3), "gelem_s": round(nn / ums / 1e6, 2), "clocks": uclk,
+                            "how": "forward sin, cos, tan + backward through autograd.Function (6 ptrig kernels "
+                                   "and torch's elementwise ops)"},
+           "fused_step": {"ms": round(fms, 3), "gelem_s": round(nn / fms / 1e6, 2),
+                          "speedup_vs_unfused": round(ums / fms, 2), "clocks": fclk},
+           "fused_kernel": {"ms": round(kms, 4), "gelem_s": round(nn / kms / 1e6, 2),
+                            "gb_s": round(20 * nn / kms / 1e6, 1), "hbm_frac": round(20 * nn / kms / 1e6 / peak, 4),
+                            "bytes_per_angle": 20, "clocks": kclk}}
+    bk = {}
+    for f, call in st["bwd"].items():
+        bms, _, bclk = _timed(call, stream, clocks)
+        bk[f"{f}_bwd_f32"] = {"ms": round(bms, 4), "gelem_s": round(nn / bms / 1e6, 2),
+                              "hbm_frac": round(12 * nn / bms / 1e6 / peak, 4), "clocks": bclk}
+    out["backward_kernels"] = bk
+    del ks, st
+    torch.cuda.empty_cache()
+    return out
+
+
+def extras(args, B, W, state, stream, peak, kernels, clocks, rank):
     import numpy as np
     import torch
 
+    x, x_host, n = state["x"], state["x_host"], state["n"]
     out = {}
     s_ptr = stream.cuda_stream
     y0 = torch.empty_like(x)
@@ -579,15 +810,15 @@ def extras(args, B, W, x, x_host, n, stream, peak, kernels):
     h1 = torch.empty_like(xh16)
     for dt, xt in (("f16", xh16), ("bf16", xbf)):
         for f in ("sin", "cos", "tan"):
-            ms = _time_call(lambda: getattr(B, f"ptrig_{f}_{dt}")(xt, h0, n, s_ptr), 5, stream)
+            ms, reps, clk = _timed(lambda: getattr(B, f"ptrig_{f}_{dt}")(xt, h0, n, s_ptr), stream, clocks, min_s=0.1)
             plain = kernels[f"{f}_f32"]["gelem_s"]
             g = n / ms / 1e6
             half[f"{f}_{dt}"] = {"ms": round(ms, 4), "gelem_s": round(g, 2), "hbm_frac": round(4 * n / ms / 1e6 / peak, 4),
-                                 "vs_plain_f32": round(g / plain, 3)}
-        ms = _time_call(lambda: getattr(B, f"ptrig_sincos_{dt}")(xt, h0, h1, n, s_ptr), 5, stream)
+                                 "vs_plain_f32": round(g / plain, 3), "clocks": clk}
+        ms, reps, clk = _timed(lambda: getattr(B, f"ptrig_sincos_{dt}")(xt, h0, h1, n, s_ptr), stream, clocks, min_s=0.1)
         g = n / ms / 1e6
         half[f"sincos_{dt}"] = {"ms": round(ms, 4), "gelem_s": round(g, 2), "hbm_frac": round(6 * n / ms / 1e6 / peak, 4),
-                                "vs_plain_f32": round(g / kernels["sincos_f32"]["gelem_s"], 3)}
+                                "vs_plain_f32": round(g / kernels["sincos_f32"]["gelem_s"], 3), "clocks": clk}
     out["packed_half"] = half
     del xh16, xbf, h0, h1
     torch.cuda.empty_cache()
@@ -603,33 +834,89 @@ def extras(args, B, W, x, x_host, n, stream, peak, kernels):
     for fi, f in enumerate(("sin", "cos", "tan")):
         ms = _time_call(lambda: B.ptrig_faithful_f64(fi, xd, yd, m, s_ptr), 5, stream)
         f64[f"faithful_{f}_f64"] = {"ms": round(ms, 4), "gelem_s": round(m / ms / 1e6, 2)}
-    out["fp64"] = {"n": m, "kernels": f64, "bound": "FP64 issue (GB300 runs FP64 at a small fraction of FP32)"}
+    # the FP64 roofline: FMA throughput of the probe kernel (events), and each
+    # kernel's FP64 FLOPs per angle (2 DFMA + DMUL + DADD, counted by ncu)
+    peak64, how = fp64_peak(B, torch, x.device, stream)
+    ops = fp64_flops()
+    for k, v in f64.items():
+        fl = ops.get(k, {}).get("flops_per_element")
+        if fl:
+            v["fp64_gflops"] = round(fl * v["gelem_s"], 1)
+            v["fp64_frac"] = round(fl * v["gelem_s"] / peak64, 4)
+            v["flops_per_element"] = fl
+    out["fp64"] = {"n": m, "kernels": f64, "bound": "FP64 issue (GB300 runs FP64 at a small fraction of FP32)",
+                   "peak_gflops": round(peak64, 1), "peak_how": how,
+                   "flops_source": "profiles/fp64_ops.json (ncu DFMA, DMUL, DADD thread instructions per angle)"}
     del xd, yd
     torch.cuda.empty_cache()
-    out["e2e"] = e2e(B, x_host, n, x.device, stream)
+    # the other configurations, each with its own event timing and clock window
+    out["large_arguments"] = leg_large(B, W, torch, x.device, stream, peak, clocks)
+    out["batch"] = leg_batch(B, W, torch, x.device, stream, peak, clocks, rank)
+    out["autograd"] = leg_autograd(B, W, torch, x.device, stream, peak, clocks, rank)
+    out["e2e"] = e2e(B, x_host, n, x.device, stream, clocks)
     out["cpu_baseline"] = oracle_rate(x_host)
     out["cpu_simd"] = cpu_simd_rate(x_host)
     return out
 
 
-def e2e(B, x_host, n, device, stream):
+def _gpu_numa_cpus(device):
+    """(NUMA node, CPU list) of the GPU from sysfs, or (None, None)."""
+    import torch
+    try:
+        p = torch.cuda.get_device_properties(device)
+        bus = f"{p.pci_domain_id:04x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
+        node = int(open(f"/sys/bus/pci/devices/{bus}/numa_node").read())
+        if node < 0:
+            return None, None
+        cpus = open(f"/sys/devices/system/node/node{node}/cpulist").read().strip()
+        return node, cpus
+    except (AttributeError, OSError, ValueError):
+        return None, None
+
+
+def _parse_cpulist(text):
+    cpus = set()
+    for part in text.split(","):
+        if "-" in part:
+            a, b = part.split("-")
+            cpus.update(range(int(a), int(b) + 1))
+        elif part:
+            cpus.add(int(part))
+    return cpus
+
+
+def e2e(B, x_host, n, device, stream, clocks):
     """The step through the C ABI with the data in pinned HOST memory, timed
-    end to end (host clock around synchronized runs of steps).  Two ways are
-    measured and the faster is reported:
+    end to end (host clock around synchronized runs of steps).  Every output
+    array of a step -- eight per step -- lands in its own pinned host buffer,
+    so every result is delivered.  The pinned buffers are allocated (and
+    first touched) from the CPUs of the GPU's NUMA node when sysfs names one.
+    Two ways are measured, three runs of 5 steps each, and the faster
+    median is reported:
       copy:      each step uploads its angles, runs the seven kernels into
                  device buffers and downloads the eight output arrays; the
                  downloads run on their own stream behind each kernel, and the
                  next step's upload goes into a second input buffer on a third
-                 stream while this step's results travel back (the two link
-                 directions are used at once).  Every step's upload and
-                 downloads are inside the timed run;
+                 stream while this step's results travel back;
       zero-copy: upload of the angles, then the seven kernels writing their
                  outputs straight into pinned host memory over NVLink-C2C (the
                  ABI takes any pointer the device can dereference)."""
     import torch
 
+    node, cpulist = _gpu_numa_cpus(device)
+    old_aff = None
+    if cpulist:
+        try:
+            old_aff = os.sched_getaffinity(0)
+            os.sched_setaffinity(0, _parse_cpulist(cpulist))
+        except OSError:
+            old_aff = None
     hx = torch.from_numpy(x_host).pin_memory()
-    hy = [torch.empty(n, dtype=torch.float32).pin_memory() for _ in range(2)]
+    hy = [torch.empty(n, dtype=torch.float32).pin_memory() for _ in range(8)]
+    for h in hy:
+        h.fill_(0)  # first touch on this node
+    if old_aff is not None:
+        os.sched_setaffinity(0, old_aff)
     dxs = [torch.empty(n, dtype=torch.float32, device=device) for _ in range(2)]
     dx = dxs[0]
     s_ptr = stream.cuda_stream
@@ -664,7 +951,7 @@ def e2e(B, x_host, n, device, stream):
         for st in range(steps):
             b = st % 2
             stream.wait_event(ready)
-            k = 0
+            k = 0  # output array index within the step: 0..7
             for name, nout in seq:
                 bufs = [(slot[0] + i) % 3 for i in range(nout)]
                 for ob in bufs:  # an output buffer is reused only after its download finished
@@ -676,7 +963,7 @@ def e2e(B, x_host, n, device, stream):
                 copy_stream.wait_event(done)
                 with torch.cuda.stream(copy_stream):
                     for ob in bufs:
-                        hy[k % 2].copy_(douts[ob], non_blocking=True)
+                        hy[k].copy_(douts[ob], non_blocking=True)
                         k += 1
                         ce = torch.cuda.Event()
                         ce.record(copy_stream)
@@ -688,26 +975,29 @@ def e2e(B, x_host, n, device, stream):
                 ready = upload(1 - b, kern_done[1 - b])
         stream.wait_stream(copy_stream)
 
-    def step_zero_copy():
-        dx.copy_(hx, non_blocking=True)
-        k = 0
-        for name, nout in seq:
-            launch(name, dx, [hy[(k + i) % 2] for i in range(nout)])
-            k += nout
-
     def run_zero_copy(steps):
         for _ in range(steps):
-            step_zero_copy()
+            dx.copy_(hx, non_blocking=True)
+            k = 0
+            for name, nout in seq:
+                launch(name, dx, hy[k:k + nout])
+                k += nout
 
-    res = {}
+    res, runs = {}, {}
+    w0 = time.perf_counter()
     for mode, run in (("copy", run_copy), ("zero-copy", run_zero_copy)):
         run(2)
         torch.cuda.synchronize()
-        reps = 5
-        t0 = time.perf_counter()
-        run(reps)
-        torch.cuda.synchronize()
-        res[mode] = (time.perf_counter() - t0) / reps
+        ts = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            run(5)
+            torch.cuda.synchronize()
+            ts.append((time.perf_counter() - t0) / 5)
+        runs[mode] = [round(t * 1e3, 3) for t in ts]
+        res[mode] = statistics.median(ts)
+    w1 = time.perf_counter()
+
     # the host link alone: one pinned copy of the angle array each way
     def link(fn):
         fn()
@@ -726,13 +1016,14 @@ def e2e(B, x_host, n, device, stream):
     bound_s = 8 * 4 * n / (d2h * 1e9)  # the step's device-to-host bytes at the link's copy rate
     return {"value": round(7 * n / dt / 1e9, 2), "unit": "Gelem/s", "h2d_bytes_per_step": 4 * n,
             "d2h_bytes_per_step": 8 * 4 * n, "ms_per_step": round(dt * 1e3, 3), "mode": best,
-            "ms_per_step_by_mode": {k: round(v * 1e3, 3) for k, v in res.items()},
+            "ms_per_step_by_mode": {k: round(v * 1e3, 3) for k, v in res.items()}, "runs_ms": runs,
             "link_gbs": {"h2d": round(h2d, 1), "d2h": round(d2h, 1)},
             "link_bound_ms": round(bound_s * 1e3, 3), "link_frac": round(bound_s / dt, 4),
-            "how": "pinned host angles -> device, the 7 kernels of the step, all 8 output arrays back in pinned "
-                   "host memory; timed with the host clock around a synchronized run of 5 steps, each step's "
-                   "upload and downloads inside it (the next step's upload overlaps this step's downloads).  link_frac = the step's "
-                   "device-to-host bytes at the measured pinned-copy rate / the measured step time"}
+            "host_numa_node": node, "host_cpus": cpulist, "clocks": clocks.window(w0, w1),
+            "how": "pinned host angles -> device, the 7 kernels of the step, each of the 8 output arrays into its "
+                   "own pinned host buffer; per mode the median of 3 runs of 5 steps, timed with the host clock "
+                   "around each synchronized run, every step's upload and downloads inside it.  link_frac = the "
+                   "step's device-to-host bytes at the measured pinned-copy rate / the step time"}
 
 
 if __name__ == "__main__":

@@ -250,3 +250,63 @@ int ptrig_cpu_f32(int func, const float *x, float *y0, float *y1, size_t n, int 
   }
   return status;
 }
+
+/* ---------------------------------------------------------- libm, context */
+
+/* The host C library's double sin / cos / tan over an array, threaded like
+ * ptrig_cpu_f32: the "inbuilt" functions the paper times its method against. */
+typedef struct {
+  int func;
+  const double *x;
+  double *y0, *y1;
+  size_t lo, hi;
+} libm_slice_t;
+
+static void *libm_slice_main(void *arg) {
+  const libm_slice_t *s = (const libm_slice_t *)arg;
+  for (size_t i = s->lo; i < s->hi; ++i) {
+    const double v = s->x[i];
+    switch (s->func) {
+      case PTRIG_CPU_SIN:
+        s->y0[i] = sin(v);
+        break;
+      case PTRIG_CPU_COS:
+        s->y0[i] = cos(v);
+        break;
+      case PTRIG_CPU_TAN:
+        s->y0[i] = tan(v);
+        break;
+      default:
+        s->y0[i] = sin(v);
+        s->y1[i] = cos(v);
+        break;
+    }
+  }
+  return NULL;
+}
+
+int ptrig_cpu_libm_f64(int func, const double *x, double *y0, double *y1, size_t n, int threads) {
+  if (func < PTRIG_CPU_SIN || func > PTRIG_CPU_SINCOS) return PTRIG_CPU_ERR_INVALID_ARG;
+  if (n == 0) return PTRIG_CPU_OK;
+  if (!x || !y0 || (func == PTRIG_CPU_SINCOS && !y1)) return PTRIG_CPU_ERR_INVALID_ARG;
+  if (threads <= 0) threads = ptrig_cpu_default_threads();
+  if (threads > 256) threads = 256;
+  if ((size_t)threads > n) threads = (int)n;
+  pthread_t tid[256];
+  libm_slice_t sl[256];
+  int started[256];
+  int status = PTRIG_CPU_OK;
+  for (int k = 0; k < threads; ++k) {
+    sl[k] = (libm_slice_t){func, x, y0, y1, n * (size_t)k / (size_t)threads, n * (size_t)(k + 1) / (size_t)threads};
+    started[k] = k > 0 && pthread_create(&tid[k], NULL, libm_slice_main, &sl[k]) == 0;
+    if (k > 0 && !started[k]) status = PTRIG_CPU_ERR_THREAD;
+  }
+  libm_slice_main(&sl[0]);
+  for (int k = 1; k < threads; ++k) {
+    if (started[k])
+      pthread_join(tid[k], NULL);
+    else
+      libm_slice_main(&sl[k]);
+  }
+  return status;
+}

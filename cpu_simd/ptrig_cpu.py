@@ -24,6 +24,9 @@ def lib():
             L.ptrig_cpu_f32.restype = ctypes.c_int
             L.ptrig_cpu_default_threads.argtypes = []
             L.ptrig_cpu_default_threads.restype = ctypes.c_int
+            L.ptrig_cpu_libm_f64.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_size_t, ctypes.c_int]
+            L.ptrig_cpu_libm_f64.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -42,4 +45,16 @@ def evaluate(func: str, x: np.ndarray, threads: int = 0, out=None):
                              None if y1 is None else y1.ctypes.data, n, threads)
     if st != 0:
         raise RuntimeError(f"ptrig_cpu_f32({func}) returned {st}")
+    return (y0, y1) if func == "sincos" else y0
+
+
+def libm(func: str, x: np.ndarray, threads: int = 0):
+    """The C library's double sin/cos/tan of x (context, not the method)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y0 = np.empty_like(x)
+    y1 = np.empty_like(x) if func == "sincos" else None
+    st = lib().ptrig_cpu_libm_f64(FUNCS[func], x.ctypes.data, y0.ctypes.data,
+                                  None if y1 is None else y1.ctypes.data, x.size, threads)
+    if st != 0:
+        raise RuntimeError(f"ptrig_cpu_libm_f64({func}) returned {st}")
     return (y0, y1) if func == "sincos" else y0

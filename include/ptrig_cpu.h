@@ -56,6 +56,12 @@ int ptrig_cpu_f32(int func, const float *x, float *y0, float *y1, size_t n, int 
 /* Number of threads ptrig_cpu_f32 uses for threads <= 0. */
 int ptrig_cpu_default_threads(void);
 
+/* For context only (not the paper's method): the host C library's double
+ * sin / cos / tan (sincos: sin into y0 and cos into y1) over x[0..n), threaded
+ * as ptrig_cpu_f32 -- the inbuilt functions the paper compares against.  The
+ * same argument checks and return codes. */
+int ptrig_cpu_libm_f64(int func, const double *x, double *y0, double *y1, size_t n, int threads);
+
 #ifdef __cplusplus
 }
 #endif

@@ -111,7 +111,23 @@ def test_header_symbols_exported(C):
     import re
     hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "ptrig_cpu.h")).read()
     names = set(re.findall(r"\b(ptrig_cpu_\w+)\s*\(", hdr))
-    assert names == {"ptrig_cpu_f32", "ptrig_cpu_default_threads"}
+    assert names == {"ptrig_cpu_f32", "ptrig_cpu_default_threads", "ptrig_cpu_libm_f64"}
     L = ctypes.CDLL(C.lib()._name)
     for nm in names:
         assert hasattr(L, nm)
+
+
+def test_libm_loop_matches_numpy_and_validates():
+    """The C library loop the bench times for context: double sin/cos/tan of
+    every element (sincos into two arrays), threaded, same argument checks."""
+    from cpu_simd import ptrig_cpu as C
+    x = np.random.default_rng(6).uniform(-1e3, 1e3, 100003)
+    for f in ("sin", "cos", "tan"):
+        assert np.allclose(C.libm(f, x, threads=5), getattr(np, f)(x), rtol=1e-12, atol=1e-12)
+    s, c = C.libm("sincos", x, threads=3)
+    assert np.allclose(s, np.sin(x), atol=1e-12) and np.allclose(c, np.cos(x), atol=1e-12)
+    L = C.lib()
+    assert L.ptrig_cpu_libm_f64(7, x.ctypes.data, x.ctypes.data, None, 4, 1) == 1
+    assert L.ptrig_cpu_libm_f64(0, None, x.ctypes.data, None, 4, 1) == 1
+    assert L.ptrig_cpu_libm_f64(3, x.ctypes.data, x.ctypes.data, None, 4, 1) == 1
+    assert L.ptrig_cpu_libm_f64(0, None, None, None, 0, 1) == 0
