@@ -142,6 +142,25 @@ def _oracle_pass(O, xd, threads):
     return time.perf_counter() - t0
 
 
+def cpu_model() -> str:
+    """The host CPU's model string (lscpu's "Model name", else /proc/cpuinfo)."""
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def oracle_rate(x_host, threads: int | None = None, full: bool = True):
     """The FP64 oracle, as it stands, over bounded samples of the workloads:
     the step's seven functions on the first 2^24 angles of the bandwidth
@@ -160,7 +179,7 @@ def oracle_rate(x_host, threads: int | None = None, full: bool = True):
     dt = _oracle_pass(O, xd, threads)
     out = {"value": 7 * m / dt / 1e9, "unit": "Gelem/s", "cores": threads, "kind": "oracle",
            "sample": f"first {m} angles of the bandwidth workload x 7 functions (sincos counted once), "
-                     f"{threads} threads, {dt:.2f} s wall"}
+                     f"{threads} threads, {dt:.2f} s wall", "cpu_model": cpu_model()}
     if not full:
         return out
     m1 = min(m, 1 << 20)
@@ -305,7 +324,7 @@ def workload_large(B, W, torch, dev, rank, log2n):
           Kernel("sincos_f32", 12 * n, n, lambda: B.ptrig_sincos_f32(x, o[0], o[1], n, s))]
     meta = {"metric": f"Gelem/s, pi/12 sin/cos/tan/sincos on 2^{n.bit_length() - 1} fp32 angles with |x| "
                       "log-uniform in [1, 1e5]",
-            "dtype": "f32 (FP64 reduction above 2^20)",
+            "dtype": "f32 (FP64 reduction above 2^19)",
             "workload": f"precision: 2^{n.bit_length() - 1} fp32 (the 2^24-angle precision mixture drawn at 4x the "
                         "size so the arrays exceed L2), |x| log-uniform in [1, 1e5], random sign; all within the "
                         "FP32 reduction range", "n_per_gpu": n,
@@ -600,12 +619,12 @@ def lookup_traffic(kernel, n, workload):
 
 def side_paths(B, torch, dev, stream, peak):
     """sin_f32 throughput of the two reduction side paths on 2^26 angles each:
-    |x| log-uniform in [2^20, 2^31) (FP64 Cody-Waite) and in [2^31, 2^127]
+    |x| log-uniform in [2^19, 2^31) (FP64 Cody-Waite) and in [2^31, 2^127]
     (Payne-Hanek)."""
     import numpy as np
     n = 1 << 26
     out = {}
-    for name, lo, hi in (("fp64_cody_waite", 20.0, 31.0), ("payne_hanek", 31.0, 127.0)):
+    for name, lo, hi in (("fp64_cody_waite", 19.0, 31.0), ("payne_hanek", 31.0, 127.0)):
         r = np.random.default_rng(7)
         xh = (2.0 ** r.uniform(lo, hi, n) * r.choice([-1.0, 1.0], n)).astype(np.float32)
         xh = np.clip(xh, -np.float32(2.0 ** hi), np.float32(2.0 ** hi))
@@ -680,13 +699,20 @@ def leg_large(B, W, torch, dev, stream, peak, clocks):
     sp = stream.cuda_stream
     x = torch.from_numpy(W.large(n)).to(dev)
     y0, y1 = torch.empty_like(x), torch.empty_like(x)
-    scratch = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 256 MiB > L2
+    scratch = torch.empty(64 << 20, dtype=torch.float32, device=dev)  # 256 MiB > L2
+    clean = torch.ones(64 << 20, dtype=torch.float32, device=dev)
+    acc = torch.empty((), dtype=torch.float32, device=dev)
 
     def flush():
-        scratch.fill_(1)
+        # write 256 MiB, then read another 256 MiB: the inputs leave L2, and the
+        # lines it holds afterwards are clean, so the timed call does not pay
+        # for writing back the flush's own dirty lines
+        scratch.fill_(1.0)
+        torch.sum(clean, out=acc)
 
     out = {"n": n, "workload": "2^24 fp32 angles, |x| log-uniform in [1, 1e5], random sign (FP32 reduction)",
-           "l2": "64 MiB arrays, L2 flushed (256 MiB write) before every timed call"}
+           "l2": "64 MiB arrays; before every timed call the L2 is flushed by a 256 MiB write followed by a "
+                 "256 MiB read (no dirty flush lines left for the timed call to write back)"}
     for f, nb in (("sin", 8), ("cos", 8), ("tan", 8), ("sincos", 12)):
         if f == "sincos":
             fn = (lambda: B.ptrig_sincos_f32(x, y0, y1, n, sp))
@@ -720,7 +746,7 @@ def leg_large(B, W, torch, dev, stream, peak, clocks):
         side[name] = {"range": f"|x| log-uniform in [2^{lo:g}, 2^{hi:g})", "ms": round(ms, 3),
                       "gelem_s": round(n / ms / 1e6, 2), "clocks": clk}
     out["side_paths_sin_f32"] = side
-    del x, y0, y1, scratch
+    del x, y0, y1, scratch, clean
     torch.cuda.empty_cache()
     return out
 
