@@ -494,19 +494,21 @@ def main():
         for k in kernels_list:
             k.call()
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-
-    # timed region: K steps, events around every kernel on the launching stream
+    # the clock sampler starts first; the warm-up steps then run right before
+    # the timed region, so that its first kernel does not start on a GPU that
+    # sat idle while the sampler came up
     nk = len(kernels_list)
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(nk + 1)] for _ in range(args.steps)]
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    # timed region: K steps, events around every kernel on the launching stream
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     wall0 = time.perf_counter()

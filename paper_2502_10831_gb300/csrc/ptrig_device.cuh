@@ -6,7 +6,6 @@
 //      with a sign; here the nearest multiple of pi/2 is taken and the paper's
 //      angle is u = t for even j, u = pi/2 - t for odd j, t = |r|):
 //        |x| <= 2^19    : FP32 Cody-Waite with FMA, 24+24+24-bit split of pi/2
-//                         (2^20 in the derivative kernels)
 //        |x| <  2^31    : FP64 Cody-Waite, 21+53+53-bit split
 //        otherwise      : Payne-Hanek, exact integer product with 2/pi
 //   2. segment  f = floor(r 12/pi) in [-4, 3] from one FMA rounded down onto
@@ -17,6 +16,8 @@
 //   3. evaluate  N = aN r + bN >= 0 and D = aD r + bD (its sign folded into
 //      the row): tan = N/D, sin = N/h, cos = D/h with h = sqrt(N^2 + D^2)
 //      (appendix A.4); sin and cos then take the quadrant sign.
+//   4. derivatives (same rows): tan' = Delta/D^2, sin' = D Delta/h^3,
+//      cos' = -N Delta/h^3 with the row's Delta = aN bD - aD bN.
 #pragma once
 
 #include <cstdint>
@@ -30,11 +31,7 @@ namespace ptrig {
 
 enum Op : int { OP_SIN = 0, OP_COS = 1, OP_TAN = 2, OP_SINCOS = 3 };
 
-// Coefficient table {aN, bN, aD, bD}, index (p << 2) | kq (see ptrig_constants.h),
-// used by the derivative kernels.
-static __constant__ float4 c_tab_f32[8] = {PTRIG_TABLE_F32};
-
-// Signed rows of the forward kernels (see ptrig_constants.h): a[i] = {aN, aD},
+// Signed rows of the FP32 kernels (see ptrig_constants.h): a[i] = {aN, aD},
 // b[i] = {bN, bD}.  Each half is 128 bytes, so a warp's 8-byte lookups from
 // shared memory never conflict (a half-warp touches each bank once at most).
 struct STab {
@@ -283,21 +280,7 @@ __device__ __forceinline__ float xor_sign(float v, uint32_t sbit) {
 
 // ------------------------------------------------------ proposed, FP32 math
 
-// kq = floor(t 12/pi) for 0 <= t < pi/3, as t 12/pi - 1/2 rounded to the
-// nearest integer by the 1.5*2^23 trick (one FFMA and one FADD on the FMA
-// pipe instead of a conversion on the XU pipe).  It differs from the floor of
-// the rounded product only where t 12/pi lies within an FP32 rounding of an
-// integer, i.e. at a node k pi/12, where both adjacent segments are valid.
-__device__ __forceinline__ uint32_t segment_kq(float t) {
-  const float z = __fmaf_rn(t, PTRIG_12_OVER_PI_F, -0.5f);
-  return __float_as_uint(__fadd_rn(z, PTRIG_RINT_MAGIC_F)) & 3u;
-}
-
-__device__ __forceinline__ uint32_t table_index(float t, uint32_t jb) {
-  return ((jb & 1u) << 2) | segment_kq(t);
-}
-
-// ------------------------------------------------- signed rows (forward)
+// ------------------------------------------------------------ signed rows
 
 // The row code of the signed-row table.  With y = M + j from the FP32
 // reduction (M = 1.5 * 2^23; the side path supplies M + (j mod 4), which has
@@ -344,6 +327,21 @@ __device__ __forceinline__ float2 seg_nd(const STab *tab, uint32_t code, float r
   return make_float2(__fmaf_rn(a.x, r, b.x), __fmaf_rn(a.y, r, b.y));
 }
 
+// Packed FP32 Cody-Waite reduction of two angles: y = M + j, r = x - j pi/2.
+template <bool TWO>
+__device__ __forceinline__ void reduce_pair(float2 x, float2 &y, float2 &r) {
+  y = __ffma2_rn(x, make_float2(PTRIG_2_OVER_PI_F, PTRIG_2_OVER_PI_F),
+                 make_float2(PTRIG_RINT_MAGIC_F, PTRIG_RINT_MAGIC_F));
+  const float2 jf = __fadd2_rn(y, make_float2(-PTRIG_RINT_MAGIC_F, -PTRIG_RINT_MAGIC_F));
+  r = __ffma2_rn(jf, make_float2(-PTRIG_PIO2_F1, -PTRIG_PIO2_F1), x);
+  if (TWO) {
+    r = __ffma2_rn(jf, make_float2(-PTRIG_PIO2_F2R, -PTRIG_PIO2_F2R), r);
+  } else {
+    r = __ffma2_rn(jf, make_float2(-PTRIG_PIO2_F2, -PTRIG_PIO2_F2), r);
+    r = __ffma2_rn(jf, make_float2(-PTRIG_PIO2_F3, -PTRIG_PIO2_F3), r);
+  }
+}
+
 // Pair form: two angles through the packed reduction, row code and radicand.
 // m0 (and m1 for sincos) are the lanes' values without the quadrant sign of
 // sin and cos; code0 / code1 carry it in bit 4 (tan needs none: the rows fold
@@ -352,16 +350,8 @@ __device__ __forceinline__ float2 seg_nd(const STab *tab, uint32_t code, float r
 template <int OP, bool TWO>
 __device__ __forceinline__ void proposed_pair(float2 x, const STab *tab, float2 &m0, float2 &m1, uint32_t &code0,
                                               uint32_t &code1) {
-  const float2 y = __ffma2_rn(x, make_float2(PTRIG_2_OVER_PI_F, PTRIG_2_OVER_PI_F),
-                              make_float2(PTRIG_RINT_MAGIC_F, PTRIG_RINT_MAGIC_F));
-  const float2 jf = __fadd2_rn(y, make_float2(-PTRIG_RINT_MAGIC_F, -PTRIG_RINT_MAGIC_F));
-  float2 r = __ffma2_rn(jf, make_float2(-PTRIG_PIO2_F1, -PTRIG_PIO2_F1), x);
-  if (TWO) {
-    r = __ffma2_rn(jf, make_float2(-PTRIG_PIO2_F2R, -PTRIG_PIO2_F2R), r);
-  } else {
-    r = __ffma2_rn(jf, make_float2(-PTRIG_PIO2_F2, -PTRIG_PIO2_F2), r);
-    r = __ffma2_rn(jf, make_float2(-PTRIG_PIO2_F3, -PTRIG_PIO2_F3), r);
-  }
+  float2 y, r;
+  reduce_pair<TWO>(x, y, r);
   const float2 v = seg_code2(r, y);
   code0 = __float_as_uint(v.x);
   code1 = __float_as_uint(v.y);
@@ -468,29 +458,72 @@ struct Taylor {
 
 // ---------------------------------------------------------- derivative, FP32
 
-// d f/dx = s_f sign(r) dF/dt, with F the Sec. 2 formula written in t
-// (N = aN t + bN, D = aD t + bD, Delta_t = aN bD - bN aD):
-//   d(N/D)/dt = Delta_t / D^2, d(N/h)/dt = D Delta_t / h^3, d(D/h)/dt = -N Delta_t / h^3.
+// On a signed row N = aN r + bN and D = aD r + bD are affine in r = x - j pi/2,
+// so with Delta = aN bD - aD bN (constant on the row) and h = sqrt(N^2 + D^2):
+//   d/dx (N / D) = Delta / D^2,  d/dx (N / h) = D Delta / h^3,
+//   d/dx (D / h) = -N Delta / h^3,
+// and the derivatives of sin and cos take the quadrant sign of the row code,
+// as sin and cos do (tan's none).
+struct RowNDL {
+  float N, D, dl;
+};
+
+__device__ __forceinline__ RowNDL seg_ndl(const STab *tab, uint32_t code, float r) {
+  const uint32_t i = code & 15u;
+  const float2 a = tab->a[i];
+  const float2 b = tab->b[i];
+  return {__fmaf_rn(a.x, r, b.x), __fmaf_rn(a.y, r, b.y), __fmaf_rn(a.x, b.y, -__fmul_rn(a.y, b.x))};
+}
+
+// Sign bit (bit 31) of the derivative of OP on the row of `code`.
+template <int OP>
+__device__ __forceinline__ uint32_t deriv_sign(uint32_t code) {
+  if (OP == OP_TAN) return 0u;
+  return seg_sign(OP == OP_SIN ? code : ~code);  // cos' = -N Delta / h^3
+}
+
+// Pair form: the derivatives of two angles without their signs, which
+// deriv_sign(code0 / code1) gives.
+template <int OP>
+__device__ __forceinline__ float2 deriv_pair(float2 x, const STab *tab, uint32_t &code0, uint32_t &code1) {
+  float2 y, r;
+  reduce_pair<false>(x, y, r);
+  const float2 v = seg_code2(r, y);
+  code0 = __float_as_uint(v.x);
+  code1 = __float_as_uint(v.y);
+  const RowNDL q0 = seg_ndl(tab, code0, r.x);
+  const RowNDL q1 = seg_ndl(tab, code1, r.y);
+  const float2 N = make_float2(q0.N, q1.N);
+  const float2 D = make_float2(q0.D, q1.D);
+  const float2 dl = make_float2(q0.dl, q1.dl);
+  if (OP == OP_TAN) {
+    const float2 rd = make_float2(rcp_approx(D.x), rcp_approx(D.y));
+    return __fmul2_rn(dl, __fmul2_rn(rd, rd));
+  }
+  const float2 h2 = __ffma2_rn(N, N, __fmul2_rn(D, D));
+  const float2 rs = make_float2(rsqrt_approx(h2.x), rsqrt_approx(h2.y));
+  const float2 rs3 = __fmul2_rn(rs, __fmul2_rn(rs, rs));
+  return __fmul2_rn(__fmul2_rn(OP == OP_SIN ? D : N, dl), rs3);
+}
+
 template <int OP>
 struct Deriv {
+  // One angle; FULL: the side paths above the FP32 reduction range.
   template <bool FULL = true>
-  __device__ __forceinline__ static float eval(float x, const float4 *tab) {
-    const RedF red = reduce_sel<FULL>(x);
-    const float t = fabsf(red.r);
-    const float4 c = tab[table_index(t, red.jb)];
-    const float N = __fmaf_rn(c.x, t, c.y);
-    const float D = __fmaf_rn(c.z, t, c.w);
-    const float dl = __fmaf_rn(c.x, c.w, -__fmul_rn(c.y, c.z));
-    const Signs g = sign_bits(red.jb, __float_as_uint(red.r));
-    const uint32_t sr = __float_as_uint(red.r) & 0x80000000u;
+  __device__ __forceinline__ static float eval(float x, const STab *tab) {
+    const RedF red = reduce_sel<FULL>(x, PTRIG_SEG_LIMIT_F);
+    const uint32_t code = seg_code(red.r, red.jb);
+    const RowNDL q = seg_ndl(tab, code, red.r);
+    float d;
     if (OP == OP_TAN) {
-      const float rd = rcp_approx(D);
-      return xor_sign(__fmul_rn(dl, __fmul_rn(rd, rd)), g.t ^ sr);
+      const float rd = rcp_approx(q.D);
+      d = __fmul_rn(q.dl, __fmul_rn(rd, rd));
+    } else {
+      const float rs = rsqrt_approx(__fmaf_rn(q.N, q.N, __fmul_rn(q.D, q.D)));
+      const float rs3 = __fmul_rn(rs, __fmul_rn(rs, rs));
+      d = __fmul_rn(__fmul_rn(OP == OP_SIN ? q.D : q.N, q.dl), rs3);
     }
-    const float rs = rsqrt_approx(__fmaf_rn(N, N, __fmul_rn(D, D)));
-    const float rs3 = __fmul_rn(rs, __fmul_rn(rs, rs));
-    if (OP == OP_SIN) return xor_sign(__fmul_rn(__fmul_rn(D, dl), rs3), g.s ^ sr);
-    return xor_sign(__fmul_rn(__fmul_rn(-N, dl), rs3), g.c ^ sr);
+    return xor_sign(d, deriv_sign<OP>(code));
   }
 };
 

@@ -124,6 +124,62 @@ def test_large_arguments(B, oracle, func):
         P.check_values(oracle, f, xd, y, ref)
 
 
+def _scattered(n, frac, seed):
+    """The bandwidth mixture with a fraction of its angles, at random
+    positions, replaced by |x| log-uniform in [2^19, 2^60) (both side paths)."""
+    x = workloads.bandwidth(n)
+    r = np.random.default_rng(seed)
+    idx = r.choice(n, max(1, int(n * frac)), replace=False)
+    x[idx] = (2.0 ** r.uniform(19.0, 60.0, idx.size) * r.choice([-1, 1], idx.size)).astype(np.float32)
+    return x
+
+
+@pytest.mark.parametrize("func", ("sin", "cos", "tan", "sincos"))
+@pytest.mark.parametrize("frac", (1e-3, 3e-2))
+def test_scattered_large_arguments(B, oracle, func, frac):
+    """Angles beyond the FP32 reduction range scattered through an ordinary
+    array (2^20 + 37 angles: whole chunks, a partial chunk and a ragged tail),
+    so that many threads meet one in the middle of their work: every output
+    against the oracle."""
+    x = _scattered((1 << 20) + 37, frac, 12)
+    xd = x.astype(np.float64)
+    seg = _segments(B, x)
+    if func == "sincos":
+        xt = _dev(x)
+        s, c = torch.empty_like(xt), torch.empty_like(xt)
+        B.ptrig_sincos_f32(xt, s, c)
+        torch.cuda.synchronize()
+        outs = {"sin": s.cpu().numpy(), "cos": c.cpu().numpy()}
+    else:
+        outs = {func: _run(B, func, x)}
+    for f, y in outs.items():
+        ref, _ = P.reference_with_gpu_segments(oracle, f, xd, seg)
+        P.check_values(oracle, f, xd, y, ref)
+
+
+@pytest.mark.parametrize("func", ("sin", "cos", "sincos"))
+def test_scattered_large_arguments_bf16(B, oracle, func):
+    """The same with bf16 storage (which holds angles up to 3.4e38): 1% of
+    2^20 + 45 angles beyond the FP32 reduction range."""
+    bits = workloads.f32_to_bf16_bits(_scattered((1 << 20) + 45, 1e-2, 13))
+    xd = workloads.bf16_bits_to_f32(bits).astype(np.float64)
+    xt = _dev(bits.view(np.int16))
+    y0 = torch.empty_like(xt)
+    if func == "sincos":
+        y1 = torch.empty_like(xt)
+        B.ptrig_sincos_bf16(xt, y0, y1)
+        outs = {"sin": y0, "cos": y1}
+    else:
+        getattr(B, f"ptrig_{func}_bf16")(xt, y0)
+        outs = {func: y0}
+    torch.cuda.synchronize()
+    seg = _segments(B, xd.astype(np.float32))
+    for f, t in outs.items():
+        got = workloads.bf16_bits_to_f32(t.cpu().numpy().view(np.uint16)).astype(np.float64)
+        ref, _ = P.reference_with_gpu_segments(oracle, f, xd, seg)
+        assert np.abs(got - ref).max() <= _half_ref_tol(f, "bf16"), (f, np.abs(got - ref).max())
+
+
 @pytest.fixture(scope="module")
 def worst_reduction():
     return P.closest_to_half_pi_multiples(oracle_module(), -1, 20, 6)
@@ -233,6 +289,28 @@ def test_bwd_f32_parity(B, oracle, func):
     x = workloads.parity(1 << 18)
     xd = x.astype(np.float64)
     g = np.random.default_rng(9).standard_normal(x.size).astype(np.float32)
+    xt, gt = _dev(x), _dev(g)
+    gx = torch.empty_like(xt)
+    getattr(B, f"ptrig_{func}_bwd_f32")(xt, gt, gx)
+    torch.cuda.synchronize()
+    got = gx.cpu().numpy().astype(np.float64)
+    u, *_ = oracle.reduce(xd)
+    keep = ~P.near_node(u)
+    if func == "tan":
+        keep &= np.abs(oracle.proposed("cos", xd)) >= 1e-3
+    ref = g.astype(np.float64) * oracle.derivative(func, xd)
+    err = np.abs(got - ref)[keep] / np.maximum(1.0, np.abs(ref[keep]))
+    assert err.max() <= 2e-5, err.max()
+
+
+@pytest.mark.parametrize("func", FUNCS)
+def test_bwd_f32_scattered_large_arguments(B, oracle, func):
+    """The derivative kernels on 2^20 + 37 angles with 1% of them beyond the
+    FP32 reduction range at random positions (whole chunks, a partial chunk
+    and a ragged tail), against the oracle's derivative."""
+    x = _scattered((1 << 20) + 37, 1e-2, 14)
+    xd = x.astype(np.float64)
+    g = np.random.default_rng(10).standard_normal(x.size).astype(np.float32)
     xt, gt = _dev(x), _dev(g)
     gx = torch.empty_like(xt)
     getattr(B, f"ptrig_{func}_bwd_f32")(xt, gt, gx)
