@@ -436,6 +436,23 @@ __global__ void __launch_bounds__(64, 16) k_chunk64_capped(const T *__restrict__
   map_chunk64<T, F, D>(x, y0, y1);
 }
 
+// fp16 sin and cos: at most 32 registers, so that 32 blocks (64 warps) fit on
+// an SM.  The fp16 kernels are latency-bound and gain from every resident
+// warp: at D <= 4 the cap costs 12-20 bytes of spill per thread (to L1) and
+// measured about 5% faster than the uncapped 38-40 registers, while fewer
+// resident blocks measured slower.  tan (more live values at D = 8) and
+// sincos stay uncapped.
+template <typename T, class F, int D>
+__global__ void __launch_bounds__(64, 32) k_chunk64_full(const T *__restrict__ x, T *__restrict__ y0,
+                                                         T *__restrict__ y1) {
+  map_chunk64<T, F, D>(x, y0, y1);
+}
+
+template <typename T, class F, int D>
+constexpr bool chunk_full_occupancy() {
+  return std::is_same<T, __half>::value && F::NOUT == 1 && F::SIGNED_OUT && D <= 4;
+}
+
 template <typename T, class F, int D, int W>
 ptrig_status launch_map_w(const LaunchCfg &c, int sms, const T *x, T *y0, T *y1, size_t n, cudaStream_t s) {
   size_t nvec = n / (Storage<T>::EPV * W);  // groups of W vectors
@@ -455,6 +472,8 @@ ptrig_status launch_map_w(const LaunchCfg &c, int sms, const T *x, T *y0, T *y1,
         if (nfull > 0) {
           if constexpr (map_capped<T, F>())
             k_chunk64_capped<T, F, D><<<(unsigned)nfull, 64, 0, s>>>(x, y0, y1);
+          else if constexpr (chunk_full_occupancy<T, F, D>())
+            k_chunk64_full<T, F, D><<<(unsigned)nfull, 64, 0, s>>>(x, y0, y1);
           else
             k_chunk64<T, F, D><<<(unsigned)nfull, 64, 0, s>>>(x, y0, y1);
           const ptrig_status st = finish_launch();
