@@ -456,7 +456,7 @@ done:
   loss_block_add<B>(acc + fast.value(), s_sum, loss);
 }
 
-constexpr int LOSS_D = 2, LOSS_L = 8;
+constexpr int LOSS_D = 2, LOSS_L = 4;
 
 ptrig_status launch_loss_f32(const float *x, const float *w, const float *v, const float *u, size_t n, float lo,
                              float hi, double *loss, float *gx, cudaStream_t s) {
