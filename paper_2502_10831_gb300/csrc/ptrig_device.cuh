@@ -64,6 +64,39 @@ __device__ __forceinline__ void st_stream(void *p, uint4 v) {
                : "memory");
 }
 
+// Asynchronous 16-byte copy global -> shared (cp.async, L2 only), its group
+// boundary and the wait for all but the N most recent groups.  The copied
+// bytes are visible to the issuing thread once its wait returns; the wait is
+// the hardware's, not a spin.  Both addresses must be 16-byte aligned.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Wait until the d-th of D committed groups (in order) has landed; d is a
+// constant once the caller's loop is unrolled, so the switch folds away.
+template <int D>
+__device__ __forceinline__ void cp_async_wait_for(int d) {
+  static_assert(D >= 1 && D <= 8, "at most eight groups");
+  switch (D - 1 - d) {
+    case 0: cp_async_wait<0>(); break;
+    case 1: cp_async_wait<1>(); break;
+    case 2: cp_async_wait<2>(); break;
+    case 3: cp_async_wait<3>(); break;
+    case 4: cp_async_wait<4>(); break;
+    case 5: cp_async_wait<5>(); break;
+    case 6: cp_async_wait<6>(); break;
+    default: cp_async_wait<7>(); break;
+  }
+}
+
 // 32-byte forms (sm_100+ .v8 accesses); p must be 32-byte aligned.
 __device__ __forceinline__ void ld_stream32(const void *p, uint4 &a, uint4 &b) {
   asm("ld.global.nc.L1::no_allocate.v8.u32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
