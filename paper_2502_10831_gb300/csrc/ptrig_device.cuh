@@ -412,9 +412,6 @@ __device__ __forceinline__ RedF reduce_sel(float x, float lim = PTRIG_FAST_LIMIT
   return red;
 }
 
-// True if x needs the FP64 / Payne-Hanek side path (or is NaN / infinite).
-__device__ __forceinline__ bool needs_slow(float x) { return !(fabsf(x) <= PTRIG_FAST_LIMIT_F); }
-
 template <int OP>
 struct Proposed {
   static constexpr int NOUT = (OP == OP_SINCOS) ? 2 : 1;
