@@ -877,6 +877,11 @@ def extras(args, B, W, state, stream, peak, kernels, clocks, rank):
             v["fp64_gflops"] = round(fl * v["gelem_s"], 1)
             v["fp64_frac"] = round(fl * v["gelem_s"] / peak64, 4)
             v["flops_per_element"] = fl
+            # DMUL and DADD take an issue slot as a DFMA does but count one
+            # FLOP: the share of the FP64 pipe's instruction rate in use
+            ins = sum(ops[k].get(o, 0.0) for o in ("dfma", "dmul", "dadd"))
+            v["fp64_inst_per_element"] = ins
+            v["fp64_pipe_frac"] = round(ins * v["gelem_s"] / (peak64 / 2), 4)
     out["fp64"] = {"n": m, "kernels": f64, "bound": "FP64 issue (GB300 runs FP64 at a small fraction of FP32)",
                    "peak_gflops": round(peak64, 1), "peak_how": how,
                    "flops_source": "profiles/fp64_ops.json (ncu DFMA, DMUL, DADD thread instructions per angle)"}
