@@ -484,6 +484,51 @@ def test_half_vector_and_scalar_paths_agree(B, dt):
                 assert np.array_equal(g, r), (dt, off)
 
 
+@pytest.mark.parametrize("dt", ["f16", "bf16"])
+def test_half_sizes_alignment_and_guard_bands(B, dt):
+    """16-bit sin, cos, tan and sincos on sizes around the whole-chunk
+    boundaries (2048 angles per fp16 chunk, 4096 per bf16 sin / cos / tan
+    chunk), aligned and misaligned: canaries around each output stay
+    untouched, and every value equals the one computed in a large aligned
+    array."""
+    canary = 0x7BCD
+    pad = 64
+    full_n = 3 * 4096 + 40
+    bits = workloads.half16(full_n).view(np.uint16) if dt == "f16" else workloads.half_bf16(full_n)
+    ref = {}
+    xt = _dev(bits.view(np.int16))
+    for f in ("sin", "cos", "tan"):
+        y = torch.empty_like(xt)
+        getattr(B, f"ptrig_{f}_{dt}")(xt, y)
+        ref[f] = y.cpu().numpy().view(np.uint16)
+    torch.cuda.synchronize()
+    for n in (0, 1, 7, 8, 9, 2047, 2048, 2049, 4095, 4096, 4097, 8200, 3 * 4096 + 5):
+        for off in (0, 3):
+            buf = np.zeros(n + 2 * pad, dtype=np.uint16)
+            buf[pad + off: pad + off + n] = bits[:n]
+            xb = _dev(buf.view(np.int16))
+            outs = {}
+            for f in ("sin", "cos", "tan", "sincos"):
+                ya = _dev(np.full(n + 2 * pad, canary, dtype=np.uint16).view(np.int16))
+                yb = _dev(np.full(n + 2 * pad, canary, dtype=np.uint16).view(np.int16))
+                xs = xb[pad + off: pad + off + n]
+                if f == "sincos":
+                    getattr(B, f"ptrig_sincos_{dt}")(xs, ya[pad + off: pad + off + n], yb[pad + off: pad + off + n], n)
+                else:
+                    getattr(B, f"ptrig_{f}_{dt}")(xs, ya[pad + off: pad + off + n], n)
+                torch.cuda.synchronize()
+                outs[f] = (ya.cpu().numpy().view(np.uint16), yb.cpu().numpy().view(np.uint16))
+            lo, hi = pad + off, pad + off + n
+            for f, (a, b) in outs.items():
+                assert np.all(a[:lo] == canary) and np.all(a[hi:] == canary), (dt, f, n, off)
+                if f == "sincos":
+                    assert np.all(b[:lo] == canary) and np.all(b[hi:] == canary), (dt, f, n, off)
+                    assert np.array_equal(a[lo:hi], ref["sin"][:n]) and np.array_equal(b[lo:hi], ref["cos"][:n])
+                else:
+                    assert np.all(b == canary)
+                    assert np.array_equal(a[lo:hi], ref[f][:n]), (dt, f, n, off)
+
+
 # -------------------------------------------------------------------- batch
 
 
