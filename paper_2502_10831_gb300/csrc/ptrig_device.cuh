@@ -575,9 +575,12 @@ __device__ __forceinline__ RedD reduce_f64(double x) {
   return {r, jb};
 }
 
+// kq = floor(t RN(12/pi)) from one FMA rounded toward -inf onto M = 1.5 * 2^52
+// (where the double's ulp is 1): an FP64 FMA instead of a multiply and a
+// conversion to integer.
 __device__ __forceinline__ uint32_t table_index_d(double t, uint32_t jb) {
-  const int kq = __double2int_rd(t * PTRIG_12_OVER_PI_D);
-  return ((jb & 1u) << 2) | ((uint32_t)kq & 3u);
+  const double c = __fma_rd(t, PTRIG_12_OVER_PI_D, PTRIG_RINT_MAGIC_D);
+  return ((jb & 1u) << 2) | ((uint32_t)__double2loint(c) & 3u);
 }
 
 // Proposed function (OP_SIN/COS/TAN) and its derivative in double.
