@@ -293,10 +293,9 @@ void ptrig_batch_plan_destroy(ptrig_batch_plan *plan);
  * counterpart in the paper: this is a library convenience.
  *
  * ptrig_batch_plan_create calls cudaMalloc and copies from the host, which
- * some callers cannot do: code running while a stream is being captured into
- * a CUDA graph, code inside an allocator or memory pool that must not call
- * back into cudaMalloc, and latency-critical paths where a device allocation
- * (which can synchronize the device) is not acceptable.  This entry point
+ * some callers cannot do: code inside an allocator or memory pool that must
+ * not call back into cudaMalloc, and latency-critical paths where a device
+ * allocation (which can synchronize the device) is not acceptable.  This entry point
  * takes the descriptors already in DEVICE memory (count ptrig_desc structs,
  * caller-owned, like the x / y arrays they point to) and calls no cudaMalloc,
  * cudaFree or other allocating routine.

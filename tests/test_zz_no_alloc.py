@@ -1,7 +1,8 @@
 """The batch entry point that allocates nothing (ptrig_batch_run_noalloc).
 
-It serves callers that may not call cudaMalloc (during stream capture, inside
-an allocator, on latency-critical paths).  Its outputs must match the
+It serves callers that may not call cudaMalloc (inside an allocator or memory
+pool, on latency-critical paths where an allocation could synchronize the
+device).  Its outputs must match the
 plan-based ptrig_batch_run within the tolerances of the parity tests, on two
 calls in a row with different batches, since the second call reuses the
 library's one scratch table.  Kept in a file that pytest collects last.
