@@ -288,8 +288,8 @@ def workload_bandwidth(B, W, torch, dev, rank, log2n):
           Kernel("taylor_sin_f32", 8 * n, n, lambda: B.ptrig_taylor_sin_f32(x, o[0], n, s)),
           Kernel("taylor_cos_f32", 8 * n, n, lambda: B.ptrig_taylor_cos_f32(x, o[0], n, s)),
           Kernel("taylor_tan_f32", 8 * n, n, lambda: B.ptrig_taylor_tan_f32(x, o[0], n, s))]
-    meta = {"metric": METRIC, "dtype": "f32", "workload": WORKLOAD, "n_per_gpu": n,
-            "l2": "inputs larger than L2 (1 GiB vs 129 MB), no flush"}
+    meta = {"metric": METRIC, "dtype": "f32", "workload": WORKLOAD.replace("2^28", f"2^{log2n}"), "n_per_gpu": n,
+            "l2": f"inputs larger than L2 ({4 * n / 2**30:g} GiB vs 129 MB), no flush"}
     return ks, meta, {"x": x, "x_host": x_host, "n": n}
 
 
@@ -305,9 +305,9 @@ def workload_half(B, W, torch, dev, rank, log2n):
         for f in ("sin", "cos", "tan"):
             ks.append(Kernel(f"{f}_{dt}", 4 * n, n, (lambda f=f, dt=dt, x=x: getattr(B, f"ptrig_{f}_{dt}")(x, o[0], n, s))))
         ks.append(Kernel(f"sincos_{dt}", 6 * n, n, (lambda dt=dt, x=x: getattr(B, f"ptrig_sincos_{dt}")(x, o[0], o[1], n, s))))
-    meta = {"metric": "Gelem/s, pi/12 sin/cos/tan/sincos on 2^28 angles stored as fp16 and bf16 (FP32 math)",
+    meta = {"metric": f"Gelem/s, pi/12 sin/cos/tan/sincos on 2^{log2n} angles stored as fp16 and bf16 (FP32 math)",
             "dtype": "f16/bf16 storage, f32 math",
-            "workload": "precision: bandwidth mixture as fp16 (uniform part |x| <= 60) and as bf16, 2^28 each; "
+            "workload": f"precision: bandwidth mixture as fp16 (uniform part |x| <= 60) and as bf16, 2^{log2n} each; "
                         "step = sin, cos, tan, sincos for both types", "n_per_gpu": n,
             "l2": "inputs larger than L2 (512 MiB vs 129 MB), no flush"}
     return ks, meta, {}
