@@ -532,15 +532,19 @@ def main():
     total_ms = R.max_over_ranks(t0.elapsed_time(t1), dist, dev)
     per_kernel_ms = [statistics.mean(ev[s][k].elapsed_time(ev[s][k + 1]) for s in range(args.steps))
                      for k in range(nk)]
+    per_kernel_med = [statistics.median(ev[s][k].elapsed_time(ev[s][k + 1]) for s in range(args.steps))
+                      for k in range(nk)]
     ms_per_step = total_ms / args.steps
     value = R.job_throughput(sum(k.elems for k in kernels_list), world, ms_per_step * 1e-3) / 1e9
     peak, peak_kind = _peaks()
     kernels = {}
-    for kern, ms in zip(kernels_list, per_kernel_ms):
+    for kern, ms, med in zip(kernels_list, per_kernel_ms, per_kernel_med):
         gbs = kern.nbytes / (ms * 1e-3) / 1e9
         kernels[kern.name] = {"ms": round(ms, 4), "gelem_s": round(kern.elems / (ms * 1e-3) / 1e9, 2),
                               "gb_s": round(gbs, 1), "hbm_frac": round(gbs / peak, 4),
-                              "hbm_frac_nominal": round(gbs / NOMINAL_HBM_GBS, 4)}
+                              "hbm_frac_nominal": round(gbs / NOMINAL_HBM_GBS, 4),
+                              "ms_median": round(med, 4),
+                              "gelem_s_median": round(kern.elems / (med * 1e-3) / 1e9, 2)}
     dom_i = max(range(nk), key=lambda k: per_kernel_ms[k])
     dom = kernels_list[dom_i]
     achieved = dom.nbytes / (per_kernel_ms[dom_i] * 1e-3) / 1e9
