@@ -165,3 +165,84 @@ def test_precision_report_large_arguments(B, oracle):
         os.makedirs(out, exist_ok=True)
         with open(os.path.join(out, "precision_report_large.json"), "w") as fh:
             json.dump(report, fh, indent=1)
+
+
+def test_precision_report_derivatives_and_fp64(B, oracle):
+    """The differentiation configuration's inputs (2^22 angles of x ~
+    U[-4pi, 4pi], w, v, u ~ N(0, 1)): each FP32 derivative kernel and the
+    fused loss kernel against the oracle's derivative and loss, away from the
+    pi/12 nodes (where the two adjacent formulas have different slopes); and
+    the FP64 forward and derivative kernels on the 2^20-angle parity set.
+    Derivative errors are |got - ref| / max(1, |ref|)."""
+    n = 1 << 22
+    x, w, v, u = (a.reshape(-1)[:n].copy() for a in workloads.autograd((8192, 512)))
+    xd = x.astype(np.float64)
+    ured, *_ = oracle.reduce(xd)
+    keep = ~P.near_node(ured)
+    idx = np.arange(n)
+    dref = {f: _threaded(lambda i: oracle.derivative(f, xd[i]), idx) for f in ("sin", "cos", "tan")}
+    cosr = np.abs(_threaded(lambda i: oracle.proposed("cos", xd[i]), idx))
+    report = {}
+    xt = torch.from_numpy(x).cuda()
+    gy = torch.ones_like(xt)
+    for f in ("sin", "cos", "tan"):
+        gx = torch.empty_like(xt)
+        getattr(B, f"ptrig_{f}_bwd_f32")(xt, gy, gx)
+        torch.cuda.synchronize()
+        got = gx.cpu().numpy().astype(np.float64)
+        k = keep & (cosr >= 1e-3) if f == "tan" else keep
+        e = np.abs(got[k] - dref[f][k]) / np.maximum(1.0, np.abs(dref[f][k]))
+        report[f"{f}_bwd_f32"] = {"max": float(e.max()), "mean": float(e.mean()), "n": int(e.size),
+                                  "kind": "|got - ref| / max(1, |ref|), away from nodes", "tolerance": 2e-5}
+        assert e.max() <= 2e-5, (f, e.max())
+    # fused loss: loss and dL/dx with clamp(tan, -50, 50)
+    lo, hi = -50.0, 50.0
+    tref = _threaded(lambda i: oracle.proposed("tan", xd[i]), idx)
+    sref = _threaded(lambda i: oracle.proposed("sin", xd[i]), idx)
+    cref = _threaded(lambda i: oracle.proposed("cos", xd[i]), idx)
+    inside = (tref >= lo) & (tref <= hi)
+    g_ref = w * dref["sin"] + v * dref["cos"] + u * dref["tan"] * inside
+    loss_ref = float(np.sum(w * sref + v * cref + u * np.clip(tref, lo, hi)))
+    wt, vt, ut = (torch.from_numpy(a).cuda() for a in (w, v, u))
+    loss = torch.zeros((), dtype=torch.float64, device="cuda")
+    gx = torch.empty_like(xt)
+    B.ptrig_sincostan_loss_f32(xt, wt, vt, ut, lo, hi, loss, gx)
+    torch.cuda.synchronize()
+    got = gx.cpu().numpy().astype(np.float64)
+    k = keep & (cosr >= 1e-3) & (np.abs(np.abs(tref) - 50.0) > 1e-2)
+    e = np.abs(got[k] - g_ref[k]) / np.maximum(1.0, np.abs(g_ref[k]))
+    rel_loss = abs(loss.item() - loss_ref) / max(1.0, abs(loss_ref))
+    report["fused_loss_f32"] = {"gradient": {"max": float(e.max()), "mean": float(e.mean()), "n": int(e.size),
+                                             "kind": "|got - ref| / max(1, |ref|), away from nodes, poles and "
+                                                     "the clamp edges"},
+                                "loss": {"relative": rel_loss, "value": loss.item(), "oracle": loss_ref}}
+    assert e.max() <= 5e-5 and abs(loss.item() - loss_ref) <= 1e-5 * max(1.0, abs(loss_ref)) + 1e-3
+    # FP64 data path on the parity set
+    xp = workloads.parity(1 << 20).astype(np.float64)
+    up, *_ = oracle.reduce(xp)
+    kp = np.abs(up - np.round(up / P.STEP) * P.STEP) >= 1e-13
+    cp = np.abs(oracle.proposed("cos", xp))
+    xpt = torch.from_numpy(xp).cuda()
+    for f in ("sin", "cos", "tan"):
+        y = torch.empty_like(xpt)
+        dy = torch.empty_like(xpt)
+        getattr(B, f"ptrig_{f}_f64")(xpt, y)
+        getattr(B, f"ptrig_{f}_bwd_f64")(xpt, torch.ones_like(xpt), dy)
+        torch.cuda.synchronize()
+        ref = oracle.proposed(f, xp)
+        dr = oracle.derivative(f, xp)
+        k = kp & (cp >= 1e-3) if f == "tan" else kp
+        yh, dyh = y.cpu().numpy(), dy.cpu().numpy()
+        ev = np.abs(yh[k] - ref[k]) / (np.abs(ref[k]) if f == "tan" else 1.0)
+        ed = np.abs(dyh[k] - dr[k]) / np.maximum(1.0, np.abs(dr[k]))
+        report[f"{f}_f64"] = {"value": {"max": float(ev.max()), "mean": float(ev.mean()),
+                                        "kind": "relative, |cos| >= 1e-3" if f == "tan" else "absolute"},
+                              "derivative": {"max": float(ed.max()), "mean": float(ed.mean()),
+                                             "kind": "|got - ref| / max(1, |ref|)"},
+                              "n": int(k.sum())}
+        assert ev.max() <= (1e-11 if f == "tan" else 1e-12) and ed.max() <= 1e-10
+    out = os.environ.get("PTRIG_REPORT_DIR")
+    if out:
+        os.makedirs(out, exist_ok=True)
+        with open(os.path.join(out, "precision_report_derivatives.json"), "w") as fh:
+            json.dump(report, fh, indent=1)
