@@ -465,6 +465,19 @@ __global__ void __launch_bounds__(64, 16) k_chunk64_capped(const T *__restrict__
   map_chunk64<T, F, D>(x, y0, y1);
 }
 
+// True when p is device (or managed) memory.  The 16-bit whole-chunk kernels
+// copy their inputs into shared memory with cp.async, which is specified for
+// device global memory; inputs in mapped host memory (which the ABI accepts)
+// take the register-staged k_map instead.
+inline bool is_device_memory(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
 template <typename T, class F, int D, int W>
 ptrig_status launch_map_w(const LaunchCfg &c, int sms, const T *x, T *y0, T *y1, size_t n, cudaStream_t s) {
   size_t nvec = n / (Storage<T>::EPV * W);  // groups of W vectors
@@ -479,7 +492,7 @@ ptrig_status launch_map_w(const LaunchCfg &c, int sms, const T *x, T *y0, T *y1,
     launch_k_map<T, F, D, true, W>((unsigned)g, c.block, s, x, y0, y1, n);
   } else {  // one-shot: one contiguous chunk of D * block groups per block
     if constexpr (W == 1 && F::USES_TABLE) {
-      if (c.block == 64) {  // whole chunks in k_chunk64, the rest in k_map
+      if (c.block == 64 && (sizeof(T) == 4 || is_device_memory(x))) {  // whole chunks in k_chunk64, the rest in k_map
         const size_t nfull = nvec / (64 * D);
         if (nfull > 0) {
           if constexpr (map_capped<T, F>())

@@ -529,6 +529,27 @@ def test_half_sizes_alignment_and_guard_bands(B, dt):
                     assert np.array_equal(a[lo:hi], ref[f][:n]), (dt, f, n, off)
 
 
+def test_mapped_host_buffers(B):
+    """Inputs and outputs in pinned host memory, which the ABI accepts (the
+    device reads and writes it over the host link): the same values as with
+    device buffers, for FP32 and both 16-bit types (whose kernels then stage
+    their inputs in registers rather than through cp.async)."""
+    n = 3 * 4096 + 40
+    cases = {"f32": workloads.bandwidth(n), "f16": workloads.half16(n).view(np.int16),
+             "bf16": workloads.half_bf16(n).view(np.int16)}
+    for dt, x in cases.items():
+        xd = _dev(x)
+        xh = torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+        for f in ("sin", "cos", "tan"):
+            yd = torch.empty_like(xd)
+            getattr(B, f"ptrig_{f}_{dt}")(xd, yd)
+            for src, dst in ((xh, torch.empty_like(xh).pin_memory()), (xh, torch.empty_like(xd)),
+                             (xd, torch.empty_like(xh).pin_memory())):
+                getattr(B, f"ptrig_{f}_{dt}")(src, dst, n)
+                torch.cuda.synchronize()
+                assert np.array_equal(dst.cpu().numpy(), yd.cpu().numpy()), (dt, f, src.is_cuda, dst.is_cuda)
+
+
 # -------------------------------------------------------------------- batch
 
 
