@@ -1,7 +1,8 @@
 // ptrig_map.cuh -- streaming elementwise kernels and their launch helper.
 //
-// Reads use ld.global.nc.L1::no_allocate and writes st.global.cs: every byte is
-// touched once, so nothing is kept in L1 and the stores are marked
+// Reads use ld.global.nc.L1::no_allocate (or, for 16-bit storage in device
+// memory, cp.async.cg into shared memory) and writes st.global.cs: every byte
+// is touched once, so nothing is kept in L1 and the stores are marked
 // evict-first in L2.  Kernels of the paper's formulas stage the 16 signed rows
 // in shared memory (two 128-byte halves read with 8-byte loads, which never
 // conflict) and move 16-byte vectors; the table-free kernels (Taylor, CUDA's
