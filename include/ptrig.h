@@ -30,8 +30,9 @@
  *   - Input semantics (the paper is silent): NaN -> NaN, +-inf -> NaN,
  *     sin(-0) = -0, tan(-0) = -0, cos(+-0) = 1.  Every finite input is
  *     reduced accurately: FP32 Cody-Waite with FMA for |x| <= 2^19 (relative
- *     error of the reduced angle below 2^-21), FP64 Cody-Waite below 2^31,
- *     Payne-Hanek (integer 2/pi product) above.
+ *     error of the reduced angle below 2^-21; with two pieces of pi/2 below
+ *     2^16 for fp16 / bf16 storage), FP64 Cody-Waite below 2^31, Payne-Hanek
+ *     (integer 2/pi product) above.
  *   - f16 / bf16 arrays are IEEE binary16 / bfloat16 bit patterns (uint16_t);
  *     the arithmetic is FP32 and the result is rounded once to the storage
  *     type.

@@ -130,6 +130,10 @@ def main() -> str:
     w(f"#define PTRIG_RINT_MAGIC_F {lit32(1.5 * 2.0 ** 23)}")
     w("/* FP32 reduction bound 2^20 of the Taylor kernels (FP64 Cody-Waite or Payne-Hanek above) */")
     w(f"#define PTRIG_FAST_LIMIT_F {lit32(2.0 ** 20)}")
+    w("/* Bound of the two-piece FP32 reduction (16-bit storage): every fp16 and")
+    w(" * bf16 value below 2^16 keeps its row code and r within 2^-21 of the")
+    w(" * three-piece reduction; larger angles take the full path */")
+    w(f"#define PTRIG_TWO_PIECE_LIMIT_F {lit32(65535.0)}")
     w("/* FP32 reduction bound of the signed-row kernels: M + 8 j stays exact")
     w(" * in [2^23, 2^24) for |j| <= 2^19 * 2/pi + 1 < 2^19 */")
     w(f"#define PTRIG_SEG_LIMIT_F {lit32(2.0 ** 19)}")

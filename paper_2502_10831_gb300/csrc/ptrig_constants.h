@@ -16,6 +16,10 @@
 #define PTRIG_RINT_MAGIC_F 0x1.8000000000000p+23f
 /* FP32 reduction bound 2^20 of the Taylor kernels (FP64 Cody-Waite or Payne-Hanek above) */
 #define PTRIG_FAST_LIMIT_F 0x1.0000000000000p+20f
+/* Bound of the two-piece FP32 reduction (16-bit storage): every fp16 and
+ * bf16 value below 2^16 keeps its row code and r within 2^-21 of the
+ * three-piece reduction; larger angles take the full path */
+#define PTRIG_TWO_PIECE_LIMIT_F 0x1.fffe000000000p+15f
 /* FP32 reduction bound of the signed-row kernels: M + 8 j stays exact
  * in [2^23, 2^24) for |j| <= 2^19 * 2/pi + 1 < 2^19 */
 #define PTRIG_SEG_LIMIT_F 0x1.0000000000000p+19f

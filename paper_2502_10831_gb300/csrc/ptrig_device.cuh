@@ -429,7 +429,7 @@ struct Proposed {
   }
   template <bool FULL = true, bool TWO = false>
   __device__ __forceinline__ static void eval(float x, const STab *tab, float &o0, float &o1) {
-    const RedF red = reduce_sel<FULL, TWO>(x, PTRIG_SEG_LIMIT_F);
+    const RedF red = reduce_sel<FULL, TWO>(x, TWO ? PTRIG_TWO_PIECE_LIMIT_F : PTRIG_SEG_LIMIT_F);
     const uint32_t code = seg_code(red.r, red.jb);
     const float2 nd = seg_nd(tab, code, red.r);
     if (OP == OP_TAN) {
@@ -677,7 +677,9 @@ template <>
 struct Storage<__nv_bfloat16> {
   static constexpr int EPV = 8;
   static constexpr bool RANGE_CHECK = true;
-  static constexpr bool TWO_PIECE = false;
+  // two pieces of pi/2 below 2^16 (checked over every such bf16 value), the
+  // full reduction from 2^16 up
+  static constexpr bool TWO_PIECE = true;
   __device__ __forceinline__ static float2 to_float2(uint32_t w) {
     __nv_bfloat162 h;
     *reinterpret_cast<uint32_t *>(&h) = w;

@@ -65,7 +65,7 @@ __device__ __forceinline__ bool map_vector_fast_h(uint4 v, size_t i, T *y0, T *y
     if constexpr (F::NOUT == 2) b[k] = S::from_float2(m1) ^ sg;
   }
   if constexpr (S::RANGE_CHECK) {
-    if (!(m <= F::limit())) return false;
+    if (!(m <= (S::TWO_PIECE ? PTRIG_TWO_PIECE_LIMIT_F : F::limit()))) return false;
   }
   st_stream(reinterpret_cast<uint4 *>(y0) + i, make_uint4(a[0], a[1], a[2], a[3]));
   if constexpr (F::NOUT == 2) st_stream(reinterpret_cast<uint4 *>(y1) + i, make_uint4(b[0], b[1], b[2], b[3]));

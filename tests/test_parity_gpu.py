@@ -124,13 +124,13 @@ def test_large_arguments(B, oracle, func):
         P.check_values(oracle, f, xd, y, ref)
 
 
-def _scattered(n, frac, seed):
+def _scattered(n, frac, seed, lo=19.0):
     """The bandwidth mixture with a fraction of its angles, at random
-    positions, replaced by |x| log-uniform in [2^19, 2^60) (both side paths)."""
+    positions, replaced by |x| log-uniform in [2^lo, 2^60) (both side paths)."""
     x = workloads.bandwidth(n)
     r = np.random.default_rng(seed)
     idx = r.choice(n, max(1, int(n * frac)), replace=False)
-    x[idx] = (2.0 ** r.uniform(19.0, 60.0, idx.size) * r.choice([-1, 1], idx.size)).astype(np.float32)
+    x[idx] = (2.0 ** r.uniform(lo, 60.0, idx.size) * r.choice([-1, 1], idx.size)).astype(np.float32)
     return x
 
 
@@ -160,8 +160,9 @@ def test_scattered_large_arguments(B, oracle, func, frac):
 @pytest.mark.parametrize("func", ("sin", "cos", "sincos"))
 def test_scattered_large_arguments_bf16(B, oracle, func):
     """The same with bf16 storage (which holds angles up to 3.4e38): 1% of
-    2^20 + 45 angles beyond the FP32 reduction range."""
-    bits = workloads.f32_to_bf16_bits(_scattered((1 << 20) + 45, 1e-2, 13))
+    2^20 + 45 angles with |x| from 2^15 up, across the 2^16 bound of the
+    two-piece reduction and the FP32 range."""
+    bits = workloads.f32_to_bf16_bits(_scattered((1 << 20) + 45, 1e-2, 13, lo=15.0))
     xd = workloads.bf16_bits_to_f32(bits).astype(np.float64)
     xt = _dev(bits.view(np.int16))
     y0 = torch.empty_like(xt)

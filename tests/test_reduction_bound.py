@@ -71,19 +71,15 @@ def _rn32(v):
     return s * Fraction(fl) / sc
 
 
-def test_two_piece_reduction_for_fp16_storage():
-    """fp16 storage reduces with two pieces of pi/2 (|x| < 2^16): over every
-    finite nonzero fp16 value, emulated exactly, the two-piece r stays within
-    2^-21 (relative) of the three-piece r and selects the same signed row,
-    so the FP32 segment dump describes the fp16 kernels too."""
+def _two_piece_worst(values):
+    """Over the given nonzero values, emulated exactly: asserts that the
+    two-piece reduction selects the same signed row as the three-piece one and
+    returns the largest relative difference of the two reduced angles."""
     c = {n: Fraction(_const(n)) for n in ("PTRIG_PIO2_F1", "PTRIG_PIO2_F2", "PTRIG_PIO2_F3", "PTRIG_PIO2_F2R",
                                           "PTRIG_2_OVER_PI_F", "PTRIG_12_OVER_PI_F", "PTRIG_RINT_MAGIC_F")}
     M = c["PTRIG_RINT_MAGIC_F"]
-    bits = np.arange(1 << 16, dtype=np.uint32).astype(np.uint16)
-    with np.errstate(invalid="ignore"):
-        xs = bits.view(np.float16).astype(np.float64)
     worst = Fraction(0)
-    for xv in xs[np.isfinite(xs) & (xs != 0)]:
+    for xv in values:
         x = Fraction(float(xv))
         y = _rn32(x * c["PTRIG_2_OVER_PI_F"] + M)
         jf = y - M
@@ -94,4 +90,34 @@ def test_two_piece_reduction_for_fp16_storage():
         assert math.floor(base + r3 * c["PTRIG_12_OVER_PI_F"]) == math.floor(base + r2 * c["PTRIG_12_OVER_PI_F"]), xv
         if r3 != 0 and jf != 0:
             worst = max(worst, abs(r2 - r3) / abs(r3))
-    assert worst < Fraction(1, 2 ** 21)
+    return worst
+
+
+def test_two_piece_limit_covers_fp16():
+    lim = _const("PTRIG_TWO_PIECE_LIMIT_F")
+    assert 65504.0 <= lim < 65536.0  # every finite fp16, no bf16 from 2^16 up
+
+
+def test_two_piece_reduction_for_bf16_storage():
+    """bf16 storage reduces with two pieces below 2^16 (larger angles take the
+    full path): over every finite nonzero bf16 value below the limit the
+    two-piece r selects the same signed row and stays within 2^-21 of the
+    three-piece r."""
+    lim = _const("PTRIG_TWO_PIECE_LIMIT_F")
+    bits = np.arange(1 << 16, dtype=np.uint32) << 16
+    with np.errstate(invalid="ignore"):
+        xs = bits.view(np.float32).astype(np.float64)
+    xs = xs[np.isfinite(xs) & (xs != 0) & (np.abs(xs) <= lim)]
+    assert xs.size > 36000
+    assert _two_piece_worst(xs) < Fraction(1, 2 ** 21)
+
+
+def test_two_piece_reduction_for_fp16_storage():
+    """fp16 storage reduces with two pieces of pi/2 (|x| < 2^16): over every
+    finite nonzero fp16 value, emulated exactly, the two-piece r stays within
+    2^-21 (relative) of the three-piece r and selects the same signed row,
+    so the FP32 segment dump describes the fp16 kernels too."""
+    bits = np.arange(1 << 16, dtype=np.uint32).astype(np.uint16)
+    with np.errstate(invalid="ignore"):
+        xs = bits.view(np.float16).astype(np.float64)
+    assert _two_piece_worst(xs[np.isfinite(xs) & (xs != 0)]) < Fraction(1, 2 ** 21)
