@@ -324,7 +324,7 @@ def workload_large(B, W, torch, dev, rank, log2n):
           Kernel("sincos_f32", 12 * n, n, lambda: B.ptrig_sincos_f32(x, o[0], o[1], n, s))]
     meta = {"metric": f"Gelem/s, pi/12 sin/cos/tan/sincos on 2^{n.bit_length() - 1} fp32 angles with |x| "
                       "log-uniform in [1, 1e5]",
-            "dtype": "f32 (FP64 reduction above 2^19)",
+            "dtype": "f32 (integer Payne-Hanek reduction above 2^19)",
             "workload": f"precision: 2^{n.bit_length() - 1} fp32 (the 2^24-angle precision mixture drawn at 4x the "
                         "size so the arrays exceed L2), |x| log-uniform in [1, 1e5], random sign; all within the "
                         "FP32 reduction range", "n_per_gpu": n,
@@ -629,13 +629,12 @@ def lookup_traffic(kernel, n, workload):
 
 
 def side_paths(B, torch, dev, stream, peak):
-    """sin_f32 throughput of the two reduction side paths on 2^26 angles each:
-    |x| log-uniform in [2^19, 2^31) (FP64 Cody-Waite) and in [2^31, 2^127]
-    (Payne-Hanek)."""
+    """sin_f32 throughput of the Payne-Hanek side path on 2^26 angles in each
+    of two ranges: |x| log-uniform in [2^19, 2^31) and in [2^31, 2^127]."""
     import numpy as np
     n = 1 << 26
     out = {}
-    for name, lo, hi in (("fp64_cody_waite", 19.0, 31.0), ("payne_hanek", 31.0, 127.0)):
+    for name, lo, hi in (("ph_2p19_2p31", 19.0, 31.0), ("ph_2p31_2p127", 31.0, 127.0)):
         r = np.random.default_rng(7)
         xh = (2.0 ** r.uniform(lo, hi, n) * r.choice([-1.0, 1.0], n)).astype(np.float32)
         xh = np.clip(xh, -np.float32(2.0 ** hi), np.float32(2.0 ** hi))
@@ -749,7 +748,7 @@ def leg_large(B, W, torch, dev, stream, peak, clocks):
     out["at_2p26"] = big
     del x4, z0, z1
     side = {}
-    for name, lo, hi in (("fp64_cody_waite", 19.0, 31.0), ("payne_hanek", 31.0, 127.0)):
+    for name, lo, hi in (("ph_2p19_2p31", 19.0, 31.0), ("ph_2p31_2p127", 31.0, 127.0)):
         r = np.random.default_rng(7)
         xh = (2.0 ** r.uniform(lo, hi, n) * r.choice([-1.0, 1.0], n)).astype(np.float32)
         x.copy_(torch.from_numpy(xh))

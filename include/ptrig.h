@@ -31,8 +31,11 @@
  *     sin(-0) = -0, tan(-0) = -0, cos(+-0) = 1.  Every finite input is
  *     reduced accurately: FP32 Cody-Waite with FMA for |x| <= 2^19 (relative
  *     error of the reduced angle below 2^-21; with two pieces of pi/2 below
- *     2^16 for fp16 / bf16 storage), FP64 Cody-Waite below 2^31, Payne-Hanek
- *     (integer 2/pi product) above.
+ *     2^16 for fp16 / bf16 storage) and Payne-Hanek above (an integer
+ *     product with 96 bits of 2/pi, the fraction scaled by pi/2 in FP32;
+ *     relative error of the reduced angle near 2^-23).  FP64 entry points:
+ *     FP64 Cody-Waite below 2^31, Payne-Hanek with an exact integer product
+ *     above.
  *   - f16 / bf16 arrays are IEEE binary16 / bfloat16 bit patterns (uint16_t);
  *     the arithmetic is FP32 and the result is rounded once to the storage
  *     type.

@@ -128,7 +128,7 @@ def main() -> str:
     w(f"#define PTRIG_PIO2_F {lit32(f32(HALF_PI))}")
     w("/* 1.5 * 2^23: adding it rounds a float to an integer held in the low mantissa bits */")
     w(f"#define PTRIG_RINT_MAGIC_F {lit32(1.5 * 2.0 ** 23)}")
-    w("/* FP32 reduction bound 2^20 of the Taylor kernels (FP64 Cody-Waite or Payne-Hanek above) */")
+    w("/* FP32 reduction bound 2^20 of the Taylor kernels (Payne-Hanek above) */")
     w(f"#define PTRIG_FAST_LIMIT_F {lit32(2.0 ** 20)}")
     w("/* Bound of the two-piece FP32 reduction (16-bit storage): every fp16 and")
     w(" * bf16 value below 2^16 keeps its row code and r within 2^-21 of the")

@@ -14,7 +14,7 @@
 #define PTRIG_PIO2_F 0x1.921fb60000000p+0f
 /* 1.5 * 2^23: adding it rounds a float to an integer held in the low mantissa bits */
 #define PTRIG_RINT_MAGIC_F 0x1.8000000000000p+23f
-/* FP32 reduction bound 2^20 of the Taylor kernels (FP64 Cody-Waite or Payne-Hanek above) */
+/* FP32 reduction bound 2^20 of the Taylor kernels (Payne-Hanek above) */
 #define PTRIG_FAST_LIMIT_F 0x1.0000000000000p+20f
 /* Bound of the two-piece FP32 reduction (16-bit storage): every fp16 and
  * bf16 value below 2^16 keeps its row code and r within 2^-21 of the

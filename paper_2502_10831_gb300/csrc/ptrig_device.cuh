@@ -6,8 +6,10 @@
 //      with a sign; here the nearest multiple of pi/2 is taken and the paper's
 //      angle is u = t for even j, u = pi/2 - t for odd j, t = |r|):
 //        |x| <= 2^19    : FP32 Cody-Waite with FMA, 24+24+24-bit split of pi/2
-//        |x| <  2^31    : FP64 Cody-Waite, 21+53+53-bit split
-//        otherwise      : Payne-Hanek, exact integer product with 2/pi
+//        FP32 beyond    : Payne-Hanek, 120-bit integer product with a 96-bit
+//                         window of 2/pi, the fraction scaled by pi/2 in FP32
+//        FP64 inputs    : FP64 Cody-Waite below 2^31 (21+53+53-bit split),
+//                         Payne-Hanek with an exact integer product above
 //   2. segment  f = floor(r 12/pi) in [-4, 3] from one FMA rounded down onto
 //      M + 8 j; the low four bits of the result, (8 j + f) mod 16, index a
 //      16-row table of the Sec. 2 formulas written in the signed r (segment
@@ -270,14 +272,70 @@ __device__ __forceinline__ double reduce_d(double x, uint32_t *jb) {
   return reduce_payne_hanek(x, jb);
 }
 
+// Payne-Hanek for a finite float with |x| >= 2^8, in integer arithmetic.
+// |x| = m 2^e with a 24-bit m (-15 <= e <= 104).  With b_k the bits of
+// 2/pi = 0.b_1 b_2 ..., the bits before b_(e-1) add multiples of 4 to
+// |x| 2/pi and the bits after b_(e+94) less than m 2^-96, so with the 96-bit
+// window W = b_(e-1) .. b_(e+94) (three funnel shifts of four table words)
+// |x| 2/pi mod 4 = P 2^-94 mod 4 for the 120-bit product P = m W: bits 94-95
+// of P are j mod 4 and bits 0-93 the fraction F, whatever e is.  F (or
+// 2^94 - F when it is at least 1/2, which rounds j up) is normalised to a
+// 64-bit g, and r = g 2^-(64 + lz) pi/2 in FP32 with pi/2 = PIO2_F1 + PIO2_F2R
+// (the first product kept exactly by an FMA): a relative error near 2^-23.
+// No FP64 operation and no indexed register array.
+static __device__ __noinline__ RedF reduce_payne_hanek_f32(float x) {
+  const uint32_t bits = __float_as_uint(x) & 0x7fffffffu;
+  const int e = (int)(bits >> 23) - 150;
+  const uint32_t m = (bits & 0x7fffffu) | 0x800000u;
+  // b_k is bit k + 31 of the table with one zero word ahead (MSB first)
+  const int t0 = e + 30;  // 15 .. 134
+  const int iw = t0 >> 5, sh = t0 & 31;
+  const uint32_t w0 = iw > 0 ? c_two_over_pi[iw - 1] : 0u;
+  const uint32_t w1 = c_two_over_pi[iw], w2 = c_two_over_pi[iw + 1], w3 = c_two_over_pi[iw + 2];
+  const uint32_t whi = __funnelshift_l(w1, w0, sh);
+  const uint32_t wmid = __funnelshift_l(w2, w1, sh);
+  const uint32_t wlo = __funnelshift_l(w3, w2, sh);
+  const uint64_t p0 = (uint64_t)m * wlo, p1 = (uint64_t)m * wmid, p2 = (uint64_t)m * whi;
+  const uint64_t lo64 = p0 + (p1 << 32);
+  const uint64_t hi64 = p2 + (p1 >> 32) + (lo64 < p0 ? 1u : 0u);  // P = hi64 2^64 + lo64
+  const uint32_t q = (uint32_t)(hi64 >> 30) & 3u;
+  uint64_t fhi = (hi64 << 34) | (lo64 >> 30);  // F bits 30 .. 93
+  uint64_t flo = lo64 & 0x3fffffffull;         // F bits 0 .. 29
+  const uint32_t up = (uint32_t)(fhi >> 63);   // fraction >= 1/2
+  if (up) {  // 2^94 - F
+    if (flo) {
+      fhi = ~fhi;
+      flo = 0x40000000ull - flo;
+    } else {
+      fhi = 0ull - fhi;
+    }
+  }
+  const int lz = min(__clzll((long long)fhi), 63);
+  const uint64_t fla = flo << 34;
+  const uint64_t g = lz ? ((fhi << lz) | (fla >> (64 - lz))) : fhi;  // fraction = g 2^-(64 + lz)
+  const float a = (float)(uint32_t)(g >> 40);                // top 24 bits, exact
+  const float b = (float)(uint32_t)((g >> 16) & 0xffffffu);  // next 24 bits, exact
+  const float hi = __fmul_rn(a, PTRIG_PIO2_F1);
+  const float err = __fmaf_rn(a, PTRIG_PIO2_F1, -hi);  // a P1 = hi + err exactly
+  const float tail = __fmaf_rn(a, PTRIG_PIO2_F2R, __fmaf_rn(__fmul_rn(b, 0x1p-24f), PTRIG_PIO2_F1, err));
+  const float scale = __int_as_float((127 - 24 - lz) << 23);  // 2^(-24 - lz)
+  float r = __fmul_rn(__fadd_rn(hi, tail), scale);
+  uint32_t jj = (q + up) & 3u;
+  if (up) r = -r;
+  if (__float_as_uint(x) >> 31) {
+    r = -r;
+    jj = (0u - jj) & 3u;
+  }
+  return {r, PTRIG_RINT_MAGIC_BITS | jj};
+}
+
 // Side path for FP32 inputs beyond the FP32 reduction range, infinities and
 // NaN.  jb holds the bits of the float M + (j mod 4), M = 1.5 * 2^23, as the
 // FP32 reduction's y = M + j does: the low bits are j mod 4 either way.
 static __device__ __noinline__ RedF reduce_slow_f32(float x) {
   if (!isfinite(x)) return {__int_as_float(0x7fffffff), PTRIG_RINT_MAGIC_BITS};
-  uint32_t jb;
-  const double r = reduce_d((double)x, &jb);
-  return {__double2float_rn(r), PTRIG_RINT_MAGIC_BITS | (jb & 3u)};
+  if (fabsf(x) < 256.0f) return reduce_fast(x);  // (not reached: callers pass |x| > 2^16)
+  return reduce_payne_hanek_f32(x);
 }
 
 __device__ __forceinline__ RedF reduce_f32(float x, float lim = PTRIG_FAST_LIMIT_F) {

@@ -123,10 +123,10 @@ __device__ __forceinline__ bool map_vector_fast(uint4 v, size_t i, T *y0, T *y1,
   return true;
 }
 
-// Vectors i, i + stride, ... < nvec with the full reduction (FP32 Cody-Waite,
-// FP64 Cody-Waite or Payne-Hanek per element).  Out of line and reached only
-// after a thread met an angle beyond the FP32 reduction range, so the
-// pipelined loop carries no call and no FP64 / Payne-Hanek register state.
+// Vectors i, i + stride, ... < nvec with the full reduction (FP32 Cody-Waite
+// or Payne-Hanek per element).  Out of line and reached only after a thread
+// met an angle beyond the fast reduction range, so the pipelined loop carries
+// no call and no Payne-Hanek register state.
 template <typename T, class F>
 static __device__ __noinline__ void map_resume_full(const T *__restrict__ x, T *__restrict__ y0,
                                                     T *__restrict__ y1, size_t i, size_t nvec, size_t stride,

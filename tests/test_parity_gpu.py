@@ -101,9 +101,9 @@ def test_edge_values(B, oracle):
 
 @pytest.mark.parametrize("func", ("sin", "cos", "tan", "sincos"))
 def test_large_arguments(B, oracle, func):
-    """|x| log-uniform in [1, 1e5] (FP32 reduction), in (2^19, 2^31) (FP64
-    Cody-Waite side path) and up to the largest float (Payne-Hanek), for every
-    function (sincos: both outputs)."""
+    """|x| log-uniform in [1, 1e5] (FP32 reduction), in (2^19, 2^31) and up
+    to the largest float (the Payne-Hanek side path), for every function
+    (sincos: both outputs)."""
     big = workloads.large(1 << 20)
     r = np.random.default_rng(4)
     mid = (2.0 ** r.uniform(19.0, 31.0, 1 << 16) * r.choice([-1, 1], 1 << 16)).astype(np.float32)
@@ -207,6 +207,32 @@ def test_reduction_worst_cases(B, oracle, worst_reduction, func):
     err = np.abs(y[small].astype(np.float64) - ref[small])
     bound = 2.0 ** -18 * np.abs(ref[small]) + 2.0 ** -149
     assert np.all(err <= bound), (func, xd[small][np.argmax(err / bound)], float((err / bound).max()))
+
+
+@pytest.mark.parametrize("func", FUNCS + ("sincos",))
+def test_side_path_worst_cases(B, oracle, func):
+    """The 6 floats of every binade [2^19, 2^27) closest to a multiple of pi/2,
+    and their negatives: they take the side path (Payne-Hanek in integer
+    arithmetic), and the result keeps the relative bound of 2^-18 wherever it
+    is small (for tan everywhere).  sincos: both outputs."""
+    x = P.closest_to_half_pi_multiples(oracle, 19, 26, 6)
+    xd = x.astype(np.float64)
+    seg = _segments(B, x)
+    if func == "sincos":
+        xt = _dev(x)
+        s, c = torch.empty_like(xt), torch.empty_like(xt)
+        B.ptrig_sincos_f32(xt, s, c)
+        torch.cuda.synchronize()
+        outs = {"sin": s.cpu().numpy(), "cos": c.cpu().numpy()}
+    else:
+        outs = {func: _run(B, func, x)}
+    for f, y in outs.items():
+        ref, _ = P.reference_with_gpu_segments(oracle, f, xd, seg)
+        P.check_values(oracle, f, xd, y, ref)
+        small = np.ones(x.shape, bool) if f == "tan" else np.abs(ref) < 1e-2
+        err = np.abs(y[small].astype(np.float64) - ref[small])
+        bound = 2.0 ** -18 * np.abs(ref[small]) + 2.0 ** -149
+        assert np.all(err <= bound), (f, xd[small][np.argmax(err / bound)], float((err / bound).max()))
 
 
 # ------------------------------------------------- sizes, alignment, in place

@@ -121,3 +121,72 @@ def test_two_piece_reduction_for_fp16_storage():
     with np.errstate(invalid="ignore"):
         xs = bits.view(np.float16).astype(np.float64)
     assert _two_piece_worst(xs[np.isfinite(xs) & (xs != 0)]) < Fraction(1, 2 ** 21)
+
+
+def _table_words():
+    h = open(HDR).read()
+    body = h[h.index("#define PTRIG_TWO_OVER_PI_WORDS"):]
+    body = body[:body.index("\n\n")] if "\n\n" in body else body
+    return [int(w, 16) for w in re.findall(r"0x([0-9a-fA-F]{8})u", body)]
+
+
+def _ph_f32_model(xv, words):
+    """The FP32 side path's Payne-Hanek steps on one float, integer steps
+    exactly and each FP32 operation rounded once: returns (r, j mod 4)."""
+    c1, c2r = Fraction(_const("PTRIG_PIO2_F1")), Fraction(_const("PTRIG_PIO2_F2R"))
+    b = int(np.float32(xv).view(np.uint32))
+    e = ((b >> 23) & 0xff) - 150
+    m = (b & 0x7fffff) | 0x800000
+    tw = [0] + list(words)  # b_k of 2/pi is bit k + 31 of this table, MSB first
+    t0 = e + 30
+    iw, sh = t0 >> 5, t0 & 31
+    window = ((tw[iw] << 96 | tw[iw + 1] << 64 | tw[iw + 2] << 32 | tw[iw + 3]) << sh >> 32) & ((1 << 96) - 1)
+    p = m * window  # 120 bits; bits 94-95 are j mod 4, bits 0-93 the fraction
+    q = (p >> 94) & 3
+    f = p & ((1 << 94) - 1)
+    up = f >> 93
+    if up:
+        f = (1 << 94) - f
+    fhi = f >> 30
+    lz = min(64 - fhi.bit_length(), 63)
+    g = (f << lz >> 30) & ((1 << 64) - 1)
+    a, bb = Fraction(g >> 40), Fraction((g >> 16) & 0xffffff)
+    hi = _rn32(a * c1)
+    tail = _rn32(a * c2r + _rn32(_rn32(bb / (1 << 24)) * c1 + (a * c1 - hi)))
+    r = _rn32(hi + tail) / Fraction(2) ** (24 + lz)
+    jj = (q + up) & 3
+    if up:
+        r = -r
+    if b >> 31:
+        r, jj = -r, (-jj) & 3
+    return r, jj
+
+
+def test_fp32_payne_hanek_model(oracle):
+    """FP32 angles beyond the fast range reduce by an integer product of the
+    24-bit significand with a 96-bit window of 2/pi: over the floats of
+    2^19 .. 2^26 closest to a multiple of pi/2, binade edges up to the largest
+    float and random angles, the model takes the nearest multiple (ties
+    aside) and the reduced angle's relative error stays below 2^-23.9 (one
+    FP32 rounding of the sum and the dropped bits of the product and of pi/2:
+    leaving out the second piece of pi/2 already gives 2^-23.2)."""
+    words = _table_words()
+    assert words[:8] == [int(w) for w in oracle.two_over_pi_words(8)]
+    half_pi = _half_pi(oracle)
+    r = np.random.default_rng(3)
+    xs = list(P.closest_to_half_pi_multiples(oracle, 19, 26, 2))
+    xs += [np.float32(2.0 ** k) for k in range(8, 128)]
+    xs += [np.nextafter(np.float32(2.0 ** k), np.float32(0)) for k in range(9, 128)]
+    xs += list((2.0 ** r.uniform(8, 127.99, 600) * r.choice([-1.0, 1.0], 600)).astype(np.float32))
+    xs.append(np.finfo(np.float32).max)
+    worst = Fraction(0)
+    for xv in xs:
+        x = Fraction(float(xv))
+        j = round(x / half_pi)
+        exact = x - j * half_pi
+        got, jj = _ph_f32_model(xv, words)
+        if jj != j % 4:  # only within rounding of an odd multiple of pi/4
+            assert abs(abs(exact) - half_pi / 2) < Fraction(1, 2 ** 20), xv
+            continue
+        worst = max(worst, abs(got - exact) / abs(exact))
+    assert math.log2(worst) < -23.9
