@@ -69,16 +69,15 @@ int occupancy(const void *kernel, int block) {
 
 // Defaults measured on GB300 (2^28 angles, sweeps of every family): the
 // table-using families run one-shot 64-thread blocks, which take the lean
-// whole-chunk kernel (k_chunk64) -- four 16-byte loads in flight per thread
-// for FP32 sin, cos and tan and for fp16 sin, cos and tan and the bf16
-// sincos, two for the FP32 sincos, eight for bf16 sin, cos and tan (at 2^24
-// angles the FP32 single-output kernels lose 10-18% with two, at 2^26-2^28
-// they gain about 1%); the fp16 sincos runs
+// whole-chunk kernel (k_chunk64) -- 16-byte loads in flight per thread: by
+// size for FP32 sin, cos and tan (four below 2^25 angles, two from there:
+// vpt_for), four for fp16 sin, cos and tan and the bf16 sincos, two for the
+// FP32 sincos, eight for bf16 sin, cos and tan; the fp16 sincos runs
 // 128-thread blocks (k_map), and so do the derivatives, with two vectors per
 // thread.  Taylor streams 32-byte groups with four in flight; CUDA's own math
 // functions run best persistent (512 threads, 8 blocks per SM).
 static std::mutex g_cfg_mu;
-static LaunchCfg g_cfg[PTRIG_FAMILY_COUNT] = {{64, 4, 0}, {64, 4, 0}, {64, 4, 0},   {128, 2, 0},
+static LaunchCfg g_cfg[PTRIG_FAMILY_COUNT] = {{64, 0, 0}, {64, 4, 0}, {64, 4, 0},   {128, 2, 0},
                                                {64, 8, 0}, {512, 2, 8}, {64, 2, 0}, {128, 4, 0},
                                                {64, 4, 0}, {64, 4, 0}, {64, 8, 0}};
 
@@ -88,7 +87,7 @@ LaunchCfg get_cfg(int family) {
 }
 
 static bool valid_cfg(int block, int vpt, int bps) {
-  return block >= 64 && block <= 512 && block % 32 == 0 && (vpt == 1 || vpt == 2 || vpt == 4 || vpt == 8) &&
+  return block >= 64 && block <= 512 && block % 32 == 0 && (vpt == 0 || vpt == 1 || vpt == 2 || vpt == 4 || vpt == 8) &&
          bps >= 0 &&
          bps <= 64;
 }

@@ -181,7 +181,7 @@ static ptrig_status launch_bwd_op(const float *x, const float *gy, float *gx, si
     k_bwd_scalar<OP><<<(unsigned)blocks, c.block, 0, s>>>(x, gy, gx, n);
     return finish_launch();
   }
-  switch (c.vpt) {
+  switch (vpt_for(c, n)) {
     case 1:
       launch_bwd_d<OP, 1>(c, sms, x, gy, gx, n, s);
       break;

@@ -13,9 +13,19 @@ namespace ptrig {
 
 struct LaunchCfg {
   int block;          // threads per block
-  int vpt;            // 16-byte loads kept in flight per thread (1, 2, 4)
+  int vpt;            // 16-byte loads kept in flight per thread (1, 2, 4, 8; 0: by size)
   int blocks_per_sm;  // > 0: persistent grid of this many blocks per SM; 0: one-shot chunks
 };
+
+// Loads in flight per thread for a call of n elements when the family's
+// setting is 0: four below 2^25 elements, whose launches are short enough
+// for the drain of the last blocks to show, two from there (measured on
+// GB300 for the FP32 kernels: at 2^24 angles four are 10-18% faster, at
+// 2^26 and 2^28 two are about 1% faster).
+constexpr size_t kVptBySizeSplit = (size_t)1 << 25;
+inline int vpt_for(const LaunchCfg &c, size_t n) {
+  return c.vpt != 0 ? c.vpt : (n >= kVptBySizeSplit ? 2 : 4);
+}
 
 LaunchCfg get_cfg(int family);
 int sm_count();                       // SMs of the current device, <= 0 if none

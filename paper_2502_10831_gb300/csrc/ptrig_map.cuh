@@ -553,7 +553,7 @@ ptrig_status launch_map(int family, const T *x, T *y0, T *y1, size_t n, cudaStre
     if (st != PTRIG_OK || head == n) return st;
     return launch_map<T, F>(family, x + head, y0 + head, F::NOUT == 2 ? y1 + head : y1, n - head, s);
   }
-  switch (c.vpt) {
+  switch (vpt_for(c, n)) {
     case 1:
       return launch_map_d<T, F, 1>(c, sms, x, y0, y1, n, s);
     case 2:

@@ -81,17 +81,20 @@ def test_launch_config_roundtrip(lib):
     old = B.ptrig_get_launch_config(B.FAMILY_TAYLOR)
     B.ptrig_set_launch_config(B.FAMILY_TAYLOR, 128, 2, 4)
     assert B.ptrig_get_launch_config(B.FAMILY_TAYLOR) == (128, 2, 4)
+    B.ptrig_set_launch_config(B.FAMILY_TAYLOR, 256, 0, 0)  # loads in flight by size
+    assert B.ptrig_get_launch_config(B.FAMILY_TAYLOR) == (256, 0, 0)
     B.ptrig_set_launch_config(B.FAMILY_TAYLOR, *old)
 
 
 def test_default_launch_configs(lib):
     """The per-family defaults picked by the GB300 sweeps: one-shot 64-thread
-    blocks (the whole-chunk kernel) with four 16-byte loads in flight (two for
-    the FP32 sincos), eight for bf16 sin, cos and tan,
+    blocks (the whole-chunk kernel) with four 16-byte loads in flight (FP32
+    sin, cos and tan by size: 0; two for the FP32 sincos), eight for bf16
+    sin, cos and tan,
     128-thread blocks for the fp16 sincos and the derivatives; the CUDA-math
     comparison kernels persistent."""
     from paper_2502_10831_gb300 import binding as B
-    want = {B.FAMILY_F32: (64, 4, 0), B.FAMILY_HALF: (64, 4, 0), B.FAMILY_TAYLOR: (64, 4, 0),
+    want = {B.FAMILY_F32: (64, 0, 0), B.FAMILY_HALF: (64, 4, 0), B.FAMILY_TAYLOR: (64, 4, 0),
             B.FAMILY_BWD: (128, 2, 0), B.FAMILY_BF16: (64, 8, 0), B.FAMILY_CUDAMATH: (512, 2, 8),
             B.FAMILY_F32_SINCOS: (64, 2, 0), B.FAMILY_HALF_SINCOS: (128, 4, 0), B.FAMILY_BF16_SINCOS: (64, 4, 0),
             B.FAMILY_HALF_TAN: (64, 4, 0), B.FAMILY_BF16_TAN: (64, 8, 0)}

@@ -16,9 +16,9 @@ torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
 
-# (threads per block, vectors per thread, blocks per SM; 0 = one-shot)
-CONFIGS = [(64, 1, 0), (64, 2, 0), (64, 4, 0), (64, 8, 0), (128, 2, 0), (128, 4, 0), (256, 4, 0), (512, 1, 0),
-           (64, 4, 2), (256, 2, 8)]
+# (threads per block, vectors per thread (0: by size), blocks per SM; 0 = one-shot)
+CONFIGS = [(64, 0, 0), (64, 1, 0), (64, 2, 0), (64, 4, 0), (64, 8, 0), (128, 2, 0), (128, 4, 0), (256, 4, 0),
+           (512, 1, 0), (64, 4, 2), (256, 2, 8)]
 N = 3 * 64 * 8 * 8 * 37 + 13
 
 
