@@ -223,7 +223,7 @@ typedef enum ptrig_family {
 
 /* Threads per block (64..512, multiple of 32), loads kept in flight per
  * thread (1, 2, 4, or 8 for fp16 / bf16; 8 acts as 4 for 4-byte types; 0
- * picks by the call's element count: 4 below 2^25 elements, 2 from there,
+ * picks by the call's element count: 4 below 2^27 elements, 2 from there,
  * the default of PTRIG_FAMILY_F32) and
  * the grid shape: blocks_per_sm = 0 launches one block per contiguous chunk
  * of block * vec_per_thread loads (one-shot); blocks_per_sm = k > 0 launches

@@ -70,7 +70,7 @@ int occupancy(const void *kernel, int block) {
 // Defaults measured on GB300 (2^28 angles, sweeps of every family): the
 // table-using families run one-shot 64-thread blocks, which take the lean
 // whole-chunk kernel (k_chunk64) -- 16-byte loads in flight per thread: by
-// size for FP32 sin, cos and tan (four below 2^25 angles, two from there:
+// size for FP32 sin, cos and tan (four below 2^27 angles, two from there:
 // vpt_for), four for fp16 sin, cos and tan and the bf16 sincos, two for the
 // FP32 sincos, eight for bf16 sin, cos and tan; the fp16 sincos runs
 // 128-thread blocks (k_map), and so do the derivatives, with two vectors per

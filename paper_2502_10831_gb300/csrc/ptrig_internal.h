@@ -18,11 +18,11 @@ struct LaunchCfg {
 };
 
 // Loads in flight per thread for a call of n elements when the family's
-// setting is 0: four below 2^25 elements, whose launches are short enough
-// for the drain of the last blocks to show, two from there (measured on
-// GB300 for the FP32 kernels: at 2^24 angles four are 10-18% faster, at
-// 2^26 and 2^28 two are about 1% faster).
-constexpr size_t kVptBySizeSplit = (size_t)1 << 25;
+// setting is 0: four below 2^27 elements, two from there.  Measured on GB300
+// for the FP32 kernels with L2 flushed before each call, four are 10%, 5% and
+// 2% faster at 2^24, 2^25 and 2^26 angles; back to back on arrays larger
+// than L2, two are 0.7% faster at 2^26 and about 1% at 2^28.
+constexpr size_t kVptBySizeSplit = (size_t)1 << 27;
 inline int vpt_for(const LaunchCfg &c, size_t n) {
   return c.vpt != 0 ? c.vpt : (n >= kVptBySizeSplit ? 2 : 4);
 }
