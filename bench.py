@@ -567,7 +567,9 @@ def main():
                   ("f32", B.FAMILY_F32), ("f32_sincos", B.FAMILY_F32_SINCOS), ("taylor", B.FAMILY_TAYLOR),
                   ("half", B.FAMILY_HALF), ("half_sincos", B.FAMILY_HALF_SINCOS), ("bf16", B.FAMILY_BF16),
                   ("bf16_sincos", B.FAMILY_BF16_SINCOS), ("half_tan", B.FAMILY_HALF_TAN),
-                  ("bf16_tan", B.FAMILY_BF16_TAN), ("bwd", B.FAMILY_BWD))}}
+                  ("bf16_tan", B.FAMILY_BF16_TAN), ("bwd", B.FAMILY_BWD))},
+              "launch_config_fields": "threads per block, 16-byte loads in flight per thread (0: four below 2^27 "
+                                      "elements, two from there), persistent blocks per SM (0: one-shot)"}
     if "autotuned" in meta:
         config["batch_autotuned"] = meta["autotuned"]
     line = {"metric": meta["metric"], "value": round(value, 2), "unit": "Gelem/s", "n_gpus": world,
